@@ -1,0 +1,285 @@
+/*
+ * lap.h -- C ABI of the GB300 solver for weighted graph Laplacian systems
+ * L x = b, preconditioned by the multilevel expanded-graph preconditioners of
+ * Hu & Lin, "Solving Graph Laplacians via Multilevel Sparsifiers".
+ *
+ * The method (citations are to the paper's sections and equations):
+ *   - the aggregation hierarchy of Section 2.2 (random-order maximal-weight
+ *     matching, leftovers join the aggregate of their heaviest neighbour,
+ *     Galerkin coarse graphs), giving P^k and the composite prolongation
+ *     P(mu) = [I, -mu P^2, ..., (-mu)^(l-1) P^l];
+ *   - the expanded Laplacian L_Gt = P(mu)^T L P(mu) (Section 3.1,
+ *     Eq. def:L_ell), its positively weighted subgraph H (PEGP, Section 3.2)
+ *     and the multilevel sparsifier T of H (MSP, Section 3.3);
+ *   - conjugate gradients on L x = b with the preconditioner
+ *     B = Pi P(mu) M P(mu)^T Pi, M = L_T^+ (MSP) or ~L_H^+ (PEGP), Pi the mean
+ *     projection.  This is the paper's expanded-system iteration (Section 4)
+ *     recast on the original n unknowns; the paper's Krylov method is FGMRES.
+ *
+ * Conventions shared by every entry point:
+ *   - Graphs are undirected, connected, given as symmetric CSR with both
+ *     directions stored, no self-loops, no duplicate entries and strictly
+ *     positive finite weights.  Vertex ids are 0-based.
+ *   - "d_" pointers are CUDA device pointers; "h_" pointers are host memory.
+ *     Vectors are contiguous FP64 arrays in the caller's vertex numbering.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is ordered on that stream; entry points that
+ *     return results on the host synchronise it.
+ *   - Right-hand sides need not have zero sum: the solver projects b onto
+ *     the range of L (mean removed) and returns the zero-mean solution.
+ *   - No entry point aborts, traps or prints.  Failures are reported by the
+ *     returned lap_status; CUDA failures map to LAP_ERR_CUDA.
+ *   - A handle may be used by one thread at a time; distinct handles are
+ *     independent.
+ */
+#ifndef LAP_H
+#define LAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lap_status {
+    LAP_OK = 0,
+    LAP_ERR_INVALID_ARG = 1,     /* bad pointer, size, option or layout       */
+    LAP_ERR_NOT_SYMMETRIC = 2,   /* CSR is not symmetric (pattern or weight)  */
+    LAP_ERR_NOT_CONNECTED = 3,   /* graph has more than one component         */
+    LAP_ERR_BAD_WEIGHT = 4,      /* weight <= 0, NaN or Inf                   */
+    LAP_ERR_OOM = 5,             /* device or host allocation failed          */
+    LAP_ERR_CUDA = 6,            /* a CUDA call failed                        */
+    LAP_ERR_NO_CONVERGENCE = 7,  /* maxit reached before the tolerance        */
+    LAP_ERR_BREAKDOWN = 8,       /* p^T L p <= 0 or a non-finite CG scalar    */
+    LAP_ERR_TIMEOUT = 9,         /* options.timeout_s elapsed                 */
+    LAP_ERR_CANCELLED = 10,      /* request cancelled (serving)               */
+    LAP_ERR_BUSY = 11,           /* no capacity (serving admission)           */
+    LAP_ERR_UNSUPPORTED = 12     /* valid request this build does not handle  */
+} lap_status;
+
+/* Preconditioner M in B = Pi P(mu) M P(mu)^T Pi. */
+typedef enum lap_prec {
+    LAP_PREC_NONE = 0,        /* B = Pi: plain conjugate gradients            */
+    LAP_PREC_MSP = 1,         /* M = L_T^+, multilevel sparsifier (Sec. 3.3)  */
+    LAP_PREC_PEGP_INNER = 2,  /* M ~= L_H^+ by an inner CG on L_H with MSP     */
+    LAP_PREC_PEGP_EXACT = 3   /* M = L_H^+ as a dense matrix (small graphs)   */
+} lap_prec;
+
+typedef enum lap_precision {
+    LAP_FP64 = 0,             /* every vector, matvec and sweep in FP64       */
+    LAP_MIXED = 1             /* FP32 matvecs/sweeps with FP32 accumulation,
+                                 FP64 dots, scalars, projection, coarsest
+                                 solve and iterative-refinement residuals    */
+} lap_precision;
+
+typedef struct lap_options {
+    int32_t prec;          /* lap_prec (default LAP_PREC_MSP)                     */
+    int32_t precision;     /* lap_precision (default LAP_FP64)                    */
+    double mu;             /* 0 < mu < 1; mu <= 0 selects 1/sqrt(n) (default 0.8) */
+    int32_t coarse_max;    /* stop coarsening once a level has <= coarse_max
+                              vertices (default 32; 2 = the paper's "level =
+                              max" with two top vertices)                          */
+    int32_t max_levels;    /* cap on the number of levels, 0 = none (default 0)   */
+    uint64_t seed;         /* seeds the random visit order (default 0)            */
+    int32_t order_random;  /* 1: visit vertices in the hashed random order;
+                              0: in increasing id order (default 1)               */
+    double tol;            /* relative residual ||Pi b - L x|| / ||Pi b||, 1e-8   */
+    int32_t maxit;         /* outer iteration cap (default 1000)                  */
+    double inner_tol;      /* PEGP_INNER: inner CG stops at ||r~|| <= inner_tol *
+                              ||r~_0|| (default 1e-2)                             */
+    int32_t inner_maxit;   /* PEGP_INNER inner iteration cap (default 200)        */
+    double refine_tol;     /* LAP_MIXED: relative tolerance of each FP32 inner
+                              solve between FP64 residual refreshes (1e-4)        */
+    int32_t max_refine;    /* LAP_MIXED: cap on refinement steps (default 20)     */
+    int32_t check_every;   /* outer iterations between host convergence polls (8) */
+    double timeout_s;      /* wall-clock limit per solve, <= 0: none (default 0)  */
+    int32_t spmv_tpr;      /* threads per CSR row in the SpMV, 0 = auto           */
+    int32_t host_only;     /* 1: build the host-side setup only and touch no GPU;
+                              only the lap_get_* queries work on such a handle  */
+    int32_t reserved[6];
+} lap_options;
+
+typedef struct lap_solve_info {
+    int32_t status;            /* lap_status of this solve                        */
+    int32_t iterations;        /* outer CG iterations (products with L)           */
+    int32_t refinements;       /* LAP_MIXED: FP64 residual refreshes              */
+    int32_t inner_iterations;  /* PEGP_INNER: total inner CG iterations           */
+    int32_t restarts;          /* restarts from a recomputed true residual        */
+    int32_t reserved0;
+    double relres;             /* true relative residual of the returned x        */
+    double relres_recurrence;  /* recurrence estimate at exit                     */
+    double seconds;            /* host wall time of the call                      */
+} lap_solve_info;
+
+#define LAP_MAX_LEVELS 64
+
+typedef struct lap_hierarchy_info {
+    int32_t levels;                     /* l                                        */
+    int32_t prec;                       /* preconditioner built at setup            */
+    int64_t n;                          /* vertices of the input graph              */
+    int64_t ntilde;                     /* vertices of the expanded graph, sum n_k  */
+    int64_t nnz;                        /* stored CSR entries of the input graph    */
+    int64_t level_size[LAP_MAX_LEVELS]; /* n_k, k = 1..l                            */
+    int64_t nnz_H;                      /* stored off-diagonal entries of L_H       */
+    int64_t edges_T;                    /* undirected edges of T                    */
+    int64_t device_bytes;               /* device memory held by the handle         */
+    double mu;                          /* the mu actually used                     */
+} lap_hierarchy_info;
+
+typedef struct lap_handle_s *lap_handle;
+
+/* Fill *opts with the defaults listed above. */
+void lap_options_default(lap_options *opts);
+
+/* Static string naming a status code; never NULL. */
+const char *lap_status_string(int32_t status);
+
+/*
+ * Route the library's device allocations through a caller allocator (for
+ * example PyTorch's caching allocator).  alloc(ctx, bytes, stream) returns a
+ * device pointer or NULL; release(ctx, ptr, stream) frees it.  Passing NULL
+ * for both restores cudaMalloc/cudaFree.  Affects allocations made after the
+ * call; set it once before the first lap_setup.
+ */
+typedef void *(*lap_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*lap_free_fn)(void *ctx, void *ptr, void *stream);
+lap_status lap_set_allocator(lap_alloc_fn alloc, lap_free_fn release, void *ctx);
+
+/*
+ * Build the solver for the graph (n, row_ptr[n+1], col_idx[nnz], w[nnz]) held
+ * in host memory (copied; the caller keeps ownership).  Validates the CSR
+ * (symmetry, weights, connectivity), builds the aggregation hierarchy
+ * (Section 2.2), the sparsifier T (Section 3.3) and, for the PEGP
+ * preconditioners, H (Section 3.2), and uploads everything to the current
+ * CUDA device on `stream`.  Requires n >= 2.  opts == NULL uses the defaults.
+ * On success *out owns device memory until lap_destroy.
+ */
+lap_status lap_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     const double *w, const lap_options *opts, void *stream,
+                     lap_handle *out);
+
+/* Release a handle and its device memory (synchronises its streams). NULL is ok. */
+void lap_destroy(lap_handle h);
+
+/* Sizes of the hierarchy built by lap_setup. */
+lap_status lap_get_hierarchy_info(lap_handle h, lap_hierarchy_info *info);
+
+/*
+ * Integer outputs of the setup, for bit-exact comparison: for level k
+ * (1 <= k < l) write agg_out[u] = id of the level-(k+1) aggregate holding
+ * level-k vertex u, both in the hierarchy's own numbering (level-1 ids are
+ * the input ids; coarse ids are aggregate creation order).  agg_out has
+ * level_size[k-1] entries.  pair_a/pair_b (optional, level_size[k] entries)
+ * receive the two matched vertices that created each aggregate.
+ */
+lap_status lap_get_aggregates(lap_handle h, int32_t level, int32_t *agg_out,
+                              int32_t *pair_a, int32_t *pair_b);
+
+/*
+ * Edge list of H (which = 0, Section 3.2) or T (which = 1, Section 3.3) in
+ * the expanded numbering: level-k vertex u has index offset_k + u with
+ * offset_k = n_1 + ... + n_{k-1} and u in the hierarchy's numbering.  Edges
+ * are written once with i < j, sorted by (i, j).  With i == NULL only *count
+ * is written.  Otherwise cap must be >= the count.  H requires a PEGP setup.
+ */
+lap_status lap_get_expanded_edges(lap_handle h, int32_t which, int64_t cap, int64_t *count,
+                                  int64_t *i, int64_t *j, double *w);
+
+/* --- device building blocks (each one step of the solve, FP64, device-resident) --- */
+
+/* d_y = L d_x (n-vectors).  Section 2.1. */
+lap_status lap_laplacian_apply(lap_handle h, const double *d_x, double *d_y, void *stream);
+
+/* d_z = B d_r = Pi P(mu) M P(mu)^T Pi d_r with the handle's preconditioner
+ * (n-vectors).  Eq. (1) preconditioner; Sections 3.2-3.3. */
+lap_status lap_precond_apply(lap_handle h, const double *d_r, double *d_z, void *stream);
+
+/* d_rt = P(mu)^T d_r: restriction to the expanded space (ntilde-vector in
+ * the expanded numbering).  Section 2.2 composite prolongation. */
+lap_status lap_restrict_apply(lap_handle h, const double *d_r, double *d_rt, void *stream);
+
+/* d_z = P(mu) d_yt: prolongation from the expanded space.  Section 2.2. */
+lap_status lap_prolong_apply(lap_handle h, const double *d_yt, double *d_z, void *stream);
+
+/* d_yt = a solution of L_T y = d_rt (d_rt must sum to zero), by elimination
+ * without fill-in over T's aggregates (Section 3.3) and a pseudo-inverse on
+ * the top level; defined up to a constant vector. */
+lap_status lap_msp_solve(lap_handle h, const double *d_rt, double *d_yt, void *stream);
+
+/* d_yt = L_H d_xt (ntilde-vectors).  Section 3.2.  Requires a PEGP setup. */
+lap_status lap_pegp_apply(lap_handle h, const double *d_xt, double *d_yt, void *stream);
+
+/* --- solves --- */
+
+/*
+ * Solve L x = b by preconditioned CG (flexible CG for PEGP_INNER) to the
+ * handle's tolerance.  d_b and d_x are device n-vectors (may not alias).
+ * Synchronises `stream` before returning.  info may be NULL.  Returns LAP_OK
+ * on convergence, LAP_ERR_NO_CONVERGENCE / LAP_ERR_BREAKDOWN /
+ * LAP_ERR_TIMEOUT with the best x so far otherwise.
+ */
+lap_status lap_pcg_solve(lap_handle h, const double *d_b, double *d_x, void *stream,
+                         lap_solve_info *info);
+
+/* Same as lap_pcg_solve with host vectors: copies b in and x out on `stream`
+ * (the copies are part of the call). */
+lap_status lap_pcg_solve_host(lap_handle h, const double *h_b, double *h_x, void *stream,
+                              lap_solve_info *info);
+
+/*
+ * Solve many systems together: graph g in [0, ng) has nrhs[g] right-hand
+ * sides stored column after column in d_B[g] (n_g * nrhs[g] doubles, column
+ * j at offset j * n_g); solutions go to d_X[g] in the same layout.  All
+ * handles must use LAP_PREC_MSP or LAP_PREC_NONE.  Every (graph, column)
+ * pair runs its own CG with its own scalars and stops on its own; the
+ * matvecs and sweeps of all pairs are batched.  infos (optional) receives
+ * sum(nrhs) entries in (graph, column) order.
+ */
+lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, const int32_t *nrhs,
+                                 const double *const *d_B, double *const *d_X, void *stream,
+                                 lap_solve_info *infos);
+
+/* --- serving: continuous batching of solve requests --- */
+
+typedef struct lap_server_s *lap_server;
+
+typedef struct lap_server_options {
+    int64_t hbm_budget_bytes;  /* admission budget for request working memory      */
+    int32_t max_slots;         /* maximum (graph, rhs) pairs in flight             */
+    int32_t check_every;       /* iterations between admission/retirement points   */
+    int32_t reserved[8];
+} lap_server_options;
+
+/* Called on the server thread when a request finishes (x already written). */
+typedef void (*lap_done_cb)(void *user, uint64_t req_id, const lap_solve_info *info);
+
+void lap_server_options_default(lap_server_options *opts);
+
+/* Start a server with its own CUDA stream and worker thread on the current device. */
+lap_status lap_server_create(const lap_server_options *opts, lap_server *out);
+
+/*
+ * Queue a request: solve L_h X = B for nrhs columns (column-major, as in
+ * lap_pcg_solve_batched; device pointers that stay valid until completion).
+ * Returns immediately with *req_id.  The request joins the running batch as
+ * soon as slots and memory allow.  h must use LAP_PREC_MSP or LAP_PREC_NONE.
+ */
+lap_status lap_serve_submit(lap_server s, lap_handle h, int32_t nrhs, const double *d_B,
+                            double *d_X, lap_done_cb cb, void *user, uint64_t *req_id);
+
+/* Block until request req_id is finished or timeout_s elapses (<= 0: forever).
+ * Writes its info.  Returns LAP_ERR_TIMEOUT if still running. */
+lap_status lap_serve_wait(lap_server s, uint64_t req_id, double timeout_s, lap_solve_info *info);
+
+/* Cancel a queued or running request (its info gets LAP_ERR_CANCELLED). */
+lap_status lap_serve_cancel(lap_server s, uint64_t req_id);
+
+/* Finish all admitted work, stop the worker and free the server. */
+void lap_server_destroy(lap_server s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAP_H */

@@ -91,6 +91,7 @@ class ExpandedOperators:
     LH: sp.csr_matrix         # Laplacian of the positive subgraph H
     LT: sp.csr_matrix         # Laplacian of the multilevel sparsifier T
     H_edges: tuple            # (i, j, weight) with i < j, sorted by (i, j)
+    H_scale: np.ndarray       # |P|^T |L| |P| at each H edge: rounding-error scale of its weight
     T_edges: tuple
     neg_edges: tuple          # the dropped edges (i < j) and their (negative) weights
 
@@ -121,10 +122,10 @@ def expanded_operators(h: Hierarchy, mu: float, *, with_LG: bool = True) -> Expa
     pos = np.searchsorted(mkey, gkey)
     assert np.all(mkey[pos] == gkey), "pattern of L_Gt must lie inside |P|^T|L||P|"
     nonzero = np.abs(gv) > ZERO_REL * mv[pos]
-    gi, gj, gv = gi[nonzero], gj[nonzero], gv[nonzero]
+    gi, gj, gv, gscale = gi[nonzero], gj[nonzero], gv[nonzero], mv[pos][nonzero]
     weight = -gv                                      # edge weight = -(off-diagonal entry)
     pos_e = weight > 0
-    Hi, Hj, Hw = gi[pos_e], gj[pos_e], weight[pos_e]
+    Hi, Hj, Hw, Hs = gi[pos_e], gj[pos_e], weight[pos_e], gscale[pos_e]
     neg = (gi[~pos_e], gj[~pos_e], weight[~pos_e])
     LH = _from_upper(nt, Hi, Hj, Hw)
 
@@ -142,4 +143,4 @@ def expanded_operators(h: Hierarchy, mu: float, *, with_LG: bool = True) -> Expa
     return ExpandedOperators(
         mu=mu, n=sizes[0], ntilde=nt, levels=len(sizes), offsets=offs, level_of=level_of,
         local_of=local_of, parent_of=parent_of, L=L, Pmu=Pmu, LG=LG if with_LG else None,
-        LH=LH, LT=LT, H_edges=(Hi, Hj, Hw), T_edges=(Ti, Tj, Tw), neg_edges=neg)
+        LH=LH, LT=LT, H_edges=(Hi, Hj, Hw), H_scale=Hs, T_edges=(Ti, Tj, Tw), neg_edges=neg)

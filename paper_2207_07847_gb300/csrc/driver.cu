@@ -1,0 +1,846 @@
+// Device upload, kernel sequencing and the CG drivers of a solver handle.
+//
+// Per CG iteration on L (Section 4 recast on n unknowns, see lap.h):
+//   k_spmv          q = L p, p.q -> alpha
+//   k_update_up1    x += alpha p, r -= alpha q, ||r|| test; level-1 restriction
+//                   and elimination of T's finest aggregates (Section 3.3)
+//   k_msp_up        levels 2 .. l-1: restriction + elimination
+//   k_coarse        top level: dense pseudo-inverse of mu^(2(l-1)) L_l
+//   k_msp_down      levels l-1 .. 2: back-substitution + Horner prolongation
+//   k_msp_down1     z = P(mu) y on level 1, sums for the projection and rho/beta
+//   k_pupdate       p = Pi z + beta p
+// captured as a CUDA graph of `check_every` iterations; every kernel returns at
+// once when the device-side convergence flag is set.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "kernels.cuh"
+#include "solver.cuh"
+
+namespace lap {
+
+#define LAP_CK(x)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (x);                                                                 \
+        if (e_ != cudaSuccess) {                                                              \
+            (void)cudaGetLastError();                                                         \
+            return e_ == cudaErrorMemoryAllocation ? LAP_ERR_OOM : LAP_ERR_CUDA;              \
+        }                                                                                     \
+    } while (0)
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int grid_for(const lap_handle_s &h, int64_t work)
+{
+    const int64_t b = (work + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(b, h.grid_cap)));
+}
+
+template <typename T>
+T *dalloc(lap_handle_s &h, size_t count)
+{
+    auto b = std::make_unique<DevBuf>();
+    if (!b->alloc(count * sizeof(T))) return nullptr;
+    T *p = b->as<T>();
+    h.device_bytes += static_cast<int64_t>(b->bytes);
+    h.bufs.push_back(std::move(b));
+    return p;
+}
+
+template <typename T, typename U>
+lap_status upload(lap_handle_s &h, T **dst, const std::vector<U> &src)
+{
+    *dst = dalloc<T>(h, std::max<size_t>(src.size(), 1));
+    if (!*dst) return LAP_ERR_OOM;
+    if (src.empty()) return LAP_OK;
+    if (std::is_same<T, U>::value) {
+        LAP_CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<T> tmp(src.begin(), src.end());
+        LAP_CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    return LAP_OK;
+}
+
+#define LAP_TRY(x)                        \
+    do {                                  \
+        lap_status s_ = (x);              \
+        if (s_ != LAP_OK) return s_;      \
+    } while (0)
+
+template <typename V>
+lap_status upload_csr(lap_handle_s &h, const HostCsr &c, DevCsr<V> &d, const DevCsr<double> *share)
+{
+    d.n = static_cast<int>(c.n);
+    d.nnz = c.rp[c.n];
+    if (share) {
+        d.rp = share->rp;
+        d.ci = share->ci;
+    } else {
+        LAP_TRY(upload(h, &d.rp, c.rp));
+        LAP_TRY(upload(h, &d.ci, c.ci));
+    }
+    LAP_TRY(upload(h, &d.w, c.w));
+    LAP_TRY(upload(h, &d.dg, c.diag));
+    return LAP_OK;
+}
+
+template <typename V>
+lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const DevMsp<double> *share)
+{
+    const int l = m.levels;
+    d.levels = l;
+    d.off.assign(m.offset.begin(), m.offset.end());
+    d.mu = static_cast<V>(m.mu);
+    d.lev.resize(static_cast<size_t>(std::max(l - 1, 0)));
+    d.gamma.resize(d.lev.size());
+    for (int k = 0; k + 1 < l; ++k) {
+        const HostMspLevel &S = m.msp[k];
+        DevMspLevel<V> &L = d.lev[k];
+        L.n = static_cast<int>(S.n);
+        L.nagg = static_cast<int>(S.nagg);
+        L.off = m.offset[k];
+        if (share) L.seg = share->lev[k].seg;
+        else LAP_TRY(upload(h, &L.seg, S.seg));
+        LAP_TRY(upload(h, &L.inv, S.inv));
+        LAP_TRY(upload(h, &L.lcf, S.lcf));
+        d.gamma[k] = static_cast<V>(m.c[k + 1] / m.c[k]);
+    }
+    d.ntop = static_cast<int>(m.lev[l - 1].n);
+    if (share) d.G = share->G;
+    else LAP_TRY(upload(h, &d.G, m.coarse_pinv));
+    return LAP_OK;
+}
+
+template <typename V>
+lap_status alloc_vectors(lap_handle_s &h, CgVectors<V> &w, int64_t n, int64_t nt, bool sweeps,
+                         bool need_T)
+{
+    w.x = dalloc<V>(h, n);
+    w.r = dalloc<V>(h, n);
+    w.p = dalloc<V>(h, n);
+    w.q = dalloc<V>(h, n);
+    w.z = dalloc<V>(h, n);
+    if (!w.x || !w.r || !w.p || !w.q || !w.z) return LAP_ERR_OOM;
+    if (sweeps) {
+        w.A = dalloc<V>(h, nt);
+        w.Y = dalloc<V>(h, nt);
+        if (!w.A || !w.Y) return LAP_ERR_OOM;
+        if (need_T) {
+            w.T = dalloc<V>(h, nt);
+            if (!w.T) return LAP_ERR_OOM;
+        }
+    }
+    return LAP_OK;
+}
+
+lap_status alloc_state(lap_handle_s &h, CgState &st)
+{
+    st.sc = dalloc<CgScalars>(h, 1);
+    st.part = dalloc<double>(h, static_cast<size_t>(kMaxRedBlocks) * kRedSlots);
+    st.ticket = dalloc<unsigned>(h, 1);
+    if (!st.sc || !st.part || !st.ticket) return LAP_ERR_OOM;
+    LAP_CK(cudaMemset(st.sc, 0, sizeof(CgScalars)));
+    LAP_CK(cudaMemset(st.ticket, 0, sizeof(unsigned)));
+    return LAP_OK;
+}
+
+int auto_tpr(double avg)
+{
+    int t = 1;
+    while (t < 32 && t < avg) t <<= 1;
+    return t;
+}
+
+// --------------------------------------------------------------------------
+// kernel sequences
+// --------------------------------------------------------------------------
+template <typename V, int MODE>
+void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, const double *bs,
+          double *yres, const CgState &st, cudaStream_t s)
+{
+    const int g = grid_for(h, static_cast<int64_t>(A.n) * tpr);
+    CgScalars *sc = st.sc;
+    double *part = st.part;
+    unsigned *tk = st.ticket;
+#define LAP_SPMV_CASE(T)                                                                             \
+    case T:                                                                                          \
+        k_spmv<V, T, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, A.dg, x, y, bs, yres, sc, part, tk); \
+        break;
+    switch (tpr) {
+        LAP_SPMV_CASE(1)
+        LAP_SPMV_CASE(2)
+        LAP_SPMV_CASE(4)
+        LAP_SPMV_CASE(8)
+        LAP_SPMV_CASE(16)
+    default:
+        k_spmv<V, 32, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, A.dg, x, y, bs, yres, sc, part, tk);
+    }
+#undef LAP_SPMV_CASE
+}
+
+// z = B r for the n-space CG (MSP sweeps, dense single level, or plain Pi).
+// With update, the CG step x += alpha p, r -= alpha q is fused in front.
+template <typename V>
+void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &w,
+                 const CgState &st, bool update, bool plain, cudaStream_t s)
+{
+    const int n = static_cast<int>(M.off[1]);
+    CgScalars *sc = st.sc;
+    if (plain || M.levels == 1) {
+        const int g = grid_for(h, n);
+#define LAP_UPD(U, P)                                                                             \
+    k_update_up1<V, U, false, P><<<g, kBlock, 0, s>>>(n, 0, nullptr, nullptr, nullptr, w.x, w.r,  \
+                                                       w.p, w.q, nullptr, nullptr, V(0), sc,      \
+                                                       st.part, st.ticket)
+        if (update && plain) LAP_UPD(true, true);
+        else if (update) LAP_UPD(true, false);
+        else if (plain) LAP_UPD(false, true);
+        else LAP_UPD(false, false);
+#undef LAP_UPD
+        if (plain) return;
+        k_dense_z<V><<<grid_for(h, int64_t(n) * 32), kBlock, 0, s>>>(n, M.G, w.r, w.q, w.z, sc, st.part,
+                                                                      st.ticket);
+        return;
+    }
+    const int l = M.levels;
+    const auto &L0 = M.lev[0];
+    if (update)
+        k_update_up1<V, true, true, false><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(
+            n, L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
+            sc, st.part, st.ticket);
+    else
+        k_update_up1<V, false, true, false><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(
+            n, L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
+            sc, st.part, st.ticket);
+    for (int k = 1; k + 1 < l; ++k) {
+        const auto &Lk = M.lev[k];
+        k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
+                                                           w.A + M.off[k], w.A + M.off[k + 1],
+                                                           M.gamma[k], nullptr, sc);
+    }
+    const int64_t ot = M.off[l - 1];
+    k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, w.A + ot, w.Y + ot,
+                                                                      w.T + ot, sc);
+    for (int k = l - 2; k >= 1; --k) {
+        const auto &Lk = M.lev[k];
+        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, w.A + M.off[k],
+                                                             w.Y + M.off[k + 1], w.T + M.off[k + 1],
+                                                             w.Y + M.off[k], w.T + M.off[k], M.mu, sc);
+    }
+    k_msp_down1<V><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(n, L0.nagg, L0.seg, w.A, w.Y + M.off[1],
+                                                          w.T + M.off[1], w.r, w.q, w.z, M.mu, sc,
+                                                          st.part, st.ticket);
+}
+
+template <typename V>
+void pupdate(const lap_handle_s &h, int64_t n, const V *z, V *p, const CgState &st, cudaStream_t s)
+{
+    k_pupdate<V><<<grid_for(h, n), kBlock, 0, s>>>(n, z, p, st.sc);
+}
+
+// Expanded-space MSP solve y~ = L_T^+ f (up to a constant): f in A (tree order,
+// overwritten), result in Y.  Section 3.3: elimination without fill-in level by
+// level, dense pseudo-inverse on the top level, back-substitution.
+template <typename V>
+void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgScalars *sc,
+               cudaStream_t s)
+{
+    const int l = M.levels;
+    for (int k = 0; k + 1 < l; ++k) {
+        const auto &Lk = M.lev[k];
+        k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
+                                                           A + M.off[k], A + M.off[k + 1], V(1),
+                                                           A + M.off[k + 1], sc);
+    }
+    const int64_t ot = M.off[l - 1];
+    k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, A + ot, Y + ot,
+                                                                      nullptr, sc);
+    for (int k = l - 2; k >= 0; --k) {
+        const auto &Lk = M.lev[k];
+        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, A + M.off[k],
+                                                             Y + M.off[k + 1], nullptr, Y + M.off[k],
+                                                             nullptr, V(0), sc);
+    }
+}
+
+// r~ = P(mu)^T r into rt and A (tree order); S is scratch for the level sums.
+template <typename V>
+void restrict_tilde(const lap_handle_s &h, const DevMsp<V> &M, const V *r, V *rt, V *A, V *S,
+                    const CgScalars *sc, cudaStream_t s)
+{
+    const int64_t n = M.off[1];
+    k_copy2<V><<<grid_for(h, n), kBlock, 0, s>>>(n, r, rt, A, sc);
+    const V *sin = r;
+    double coef = 1.0;
+    for (int k = 0; k + 1 < M.levels; ++k) {
+        const auto &Lk = M.lev[k];
+        coef *= -static_cast<double>(M.mu);
+        V *sout = S + M.off[k + 1];
+        k_restrict_level<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(
+            Lk.nagg, Lk.seg, sin, sout, rt + M.off[k + 1], A ? A + M.off[k + 1] : nullptr,
+            static_cast<V>(coef), sc);
+        sin = sout;
+    }
+}
+
+// t = P(mu) y~ by Horner from the top (tree order): T holds t_k on levels >= 2;
+// the finest level goes through k_msp_down1 with the outer CG's reductions.
+template <typename V>
+void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, V *T,
+                        const CgVectors<V> &w, const CgState &st, cudaStream_t s)
+{
+    const int l = M.levels;
+    const int64_t ot = M.off[l - 1];
+    k_copy2<V><<<grid_for(h, M.ntop), kBlock, 0, s>>>(M.ntop, yt + ot, T + ot, nullptr, st.sc);
+    for (int k = l - 2; k >= 1; --k) {
+        const auto &Lk = M.lev[k];
+        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, yt + M.off[k], nullptr,
+                                                             T + M.off[k + 1], nullptr, T + M.off[k],
+                                                             M.mu, st.sc);
+    }
+    const auto &L0 = M.lev[0];
+    k_msp_down1<V><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(static_cast<int>(M.off[1]), L0.nagg, L0.seg,
+                                                          yt, nullptr, T + M.off[1], w.r, w.q, w.z,
+                                                          M.mu, st.sc, st.part, st.ticket);
+}
+
+// One expanded-space CG iteration of the PEGP inner solve L_H y~ = r~ with the
+// MSP preconditioner (vectors e: x = y~, r = r~, p, q, z unused, A/Y sweeps).
+template <typename V>
+void inner_iteration(const lap_handle_s &h, const DevCsr<V> &H, const DevMsp<V> &M,
+                     const CgVectors<V> &e, const CgState &st, cudaStream_t s)
+{
+    const int64_t nt = M.off[M.levels];
+    spmv<V, 0>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
+    k_update_up1<V, true, false, false><<<grid_for(h, nt), kBlock, 0, s>>>(
+        static_cast<int>(nt), 0, nullptr, nullptr, nullptr, e.x, e.r, e.p, e.q, e.A, nullptr, V(0),
+        st.sc, st.part, st.ticket);
+    msp_tilde<V>(h, M, e.A, e.Y, st.sc, s);
+    k_zred<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.Y, e.r, st.sc, st.part, st.ticket);
+    pupdate<V>(h, nt, e.Y, e.p, st, s);
+}
+
+// Start of the inner solve: y~ = 0, z~ = MSP(r~), p~ = Pi z~ (A holds r~).
+template <typename V>
+void inner_start(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &e, const CgState &st,
+                 double tol, int maxit, cudaStream_t s)
+{
+    const int64_t nt = M.off[M.levels];
+    k_cg_reset<<<1, 1, 0, s>>>(st.sc, tol, maxit, 0);
+    k_vec_init<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.r, e.x, st.sc, st.part, st.ticket);
+    msp_tilde<V>(h, M, e.A, e.Y, st.sc, s);
+    k_zred<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.Y, e.r, st.sc, st.part, st.ticket);
+    pupdate<V>(h, nt, e.Y, e.p, st, s);
+}
+
+template <typename V> struct Sel;
+template <> struct Sel<double> {
+    static const DevCsr<double> &L(const lap_handle_s &h) { return h.L64; }
+    static const DevCsr<double> &H(const lap_handle_s &h) { return h.H64; }
+    static const DevMsp<double> &M(const lap_handle_s &h) { return h.M64; }
+    static const CgVectors<double> &w(const lap_handle_s &h) { return h.w64; }
+    static const CgVectors<double> &e(const lap_handle_s &h) { return h.e64; }
+    static const CgState &st(const lap_handle_s &h) { return h.st64; }
+    static const CgState &ste(const lap_handle_s &h) { return h.ste64; }
+    static cudaGraphExec_t &gi(lap_handle_s &h) { return h.g_iter64; }
+    static cudaGraphExec_t &gin(lap_handle_s &h) { return h.g_in64; }
+};
+template <> struct Sel<float> {
+    static const DevCsr<float> &L(const lap_handle_s &h) { return h.L32; }
+    static const DevCsr<float> &H(const lap_handle_s &h) { return h.H32; }
+    static const DevMsp<float> &M(const lap_handle_s &h) { return h.M32; }
+    static const CgVectors<float> &w(const lap_handle_s &h) { return h.w32; }
+    static const CgVectors<float> &e(const lap_handle_s &h) { return h.e32; }
+    static const CgState &st(const lap_handle_s &h) { return h.st32; }
+    static const CgState &ste(const lap_handle_s &h) { return h.ste32; }
+    static cudaGraphExec_t &gi(lap_handle_s &h) { return h.g_iter32; }
+    static cudaGraphExec_t &gin(lap_handle_s &h) { return h.g_in32; }
+};
+
+bool is_plain(const lap_handle_s &h) { return h.m.opt.prec == LAP_PREC_NONE; }
+bool is_pegp(const lap_handle_s &h) { return h.m.opt.prec == LAP_PREC_PEGP_INNER; }
+
+// one outer CG iteration for the graph-captured preconditioners (MSP, none)
+template <typename V>
+void outer_iteration(const lap_handle_s &h, cudaStream_t s)
+{
+    const auto &w = Sel<V>::w(h);
+    const auto &st = Sel<V>::st(h);
+    spmv<V, 0>(h, Sel<V>::L(h), h.tpr, w.p, w.q, nullptr, nullptr, st, s);
+    precond_msp<V>(h, Sel<V>::M(h), w, st, true, is_plain(h), s);
+    pupdate<V>(h, Sel<V>::M(h).off[1], is_plain(h) ? w.r : w.z, w.p, st, s);
+}
+
+template <typename Fn>
+lap_status capture(lap_handle_s &h, cudaGraphExec_t &g, Fn body)
+{
+    cudaGraph_t graph = nullptr;
+    LAP_CK(cudaStreamBeginCapture(h.s, cudaStreamCaptureModeThreadLocal));
+    body();
+    cudaError_t e = cudaStreamEndCapture(h.s, &graph);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LAP_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        g = nullptr;
+        return LAP_ERR_CUDA;
+    }
+    return LAP_OK;
+}
+
+lap_status poll(lap_handle_s &h, const CgState &st, CgScalars &out)
+{
+    LAP_CK(cudaMemcpyAsync(h.hsc, st.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, h.s));
+    LAP_CK(cudaStreamSynchronize(h.s));
+    out = *h.hsc;
+    return LAP_OK;
+}
+
+bool timed_out(const lap_handle_s &h, Clock::time_point t0)
+{
+    return h.m.opt.timeout_s > 0.0 &&
+           std::chrono::duration<double>(Clock::now() - t0).count() > h.m.opt.timeout_s;
+}
+
+// Preconditioner application B r for the outer CG (fresh start or after an
+// update).  For PEGP_INNER this runs the inner CG with host polling.
+template <typename V>
+lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int &inner_total)
+{
+    const cudaStream_t s = h.s;
+    const auto &w = Sel<V>::w(h);
+    const auto &st = Sel<V>::st(h);
+    const auto &M = Sel<V>::M(h);
+    const int64_t n = M.off[1];
+    if (!is_pegp(h)) {
+        precond_msp<V>(h, M, w, st, update, is_plain(h), s);
+        return LAP_OK;
+    }
+    if (update)
+        k_update_up1<V, true, false, false><<<grid_for(h, n), kBlock, 0, s>>>(
+            static_cast<int>(n), 0, nullptr, nullptr, nullptr, w.x, w.r, w.p, w.q, nullptr, nullptr,
+            V(0), st.sc, st.part, st.ticket);
+    CgScalars sc;
+    LAP_TRY(poll(h, st, sc));
+    if (sc.flag != kRun) return LAP_OK;          // converged / stopped: nothing to apply
+    const auto &e = Sel<V>::e(h);
+    const auto &ste = Sel<V>::ste(h);
+    restrict_tilde<V>(h, M, w.r, e.r, e.A, e.T, nullptr, s);
+    inner_start<V>(h, M, e, ste, h.m.opt.inner_tol, h.m.opt.inner_maxit, s);
+    cudaGraphExec_t &g = Sel<V>::gin(h);
+    const int K = std::max(1, std::min(h.m.opt.check_every, 16));
+    if (!g) {
+        LAP_TRY(capture(h, g, [&] {
+            for (int i = 0; i < K; ++i) inner_iteration<V>(h, Sel<V>::H(h), M, e, ste, s);
+        }));
+    }
+    // the device stops at inner_maxit; the launch cap only guards the host loop
+    const int cap_in = h.m.opt.inner_maxit / K + 4;
+    for (int launches = 0;; ++launches) {
+        LAP_CK(cudaGraphLaunch(g, s));
+        CgScalars si;
+        LAP_TRY(poll(h, ste, si));
+        if (si.flag != kRun) {
+            inner_total += si.iter;
+            break;
+        }
+        if (launches >= cap_in) return LAP_ERR_BREAKDOWN;
+        if (timed_out(h, t0)) return LAP_ERR_TIMEOUT;
+    }
+    prolong_tilde_to_z<V>(h, M, e.x, e.T, w, st, s);
+    return LAP_OK;
+}
+
+// CG iterations on the current system until the device flag stops them.
+template <typename V>
+lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgScalars &sc)
+{
+    const cudaStream_t s = h.s;
+    const auto &w = Sel<V>::w(h);
+    const auto &st = Sel<V>::st(h);
+    const int64_t n = Sel<V>::M(h).off[1];
+    if (is_pegp(h)) {
+        for (int guard = 0; guard <= h.m.opt.maxit + 4; ++guard) {
+            spmv<V, 0>(h, Sel<V>::L(h), h.tpr, w.p, w.q, nullptr, nullptr, st, s);
+            LAP_TRY(apply_precond<V>(h, true, t0, inner_total));
+            pupdate<V>(h, n, w.z, w.p, st, s);
+            LAP_TRY(poll(h, st, sc));
+            if (sc.flag != kRun) return LAP_OK;
+            if (timed_out(h, t0)) return LAP_ERR_TIMEOUT;
+        }
+        return LAP_ERR_BREAKDOWN;
+    }
+    cudaGraphExec_t &g = Sel<V>::gi(h);
+    if (!g) LAP_TRY(capture(h, g, [&] {
+            for (int i = 0; i < h.m.opt.check_every; ++i) outer_iteration<V>(h, s);
+        }));
+    // the device stops at maxit; the launch cap only guards the host loop
+    const int cap = h.m.opt.maxit / h.m.opt.check_every + 4;
+    for (int launches = 0;; ++launches) {
+        LAP_CK(cudaGraphLaunch(g, s));
+        LAP_TRY(poll(h, st, sc));
+        if (sc.flag != kRun) return LAP_OK;
+        if (launches >= cap) return LAP_ERR_BREAKDOWN;
+        if (timed_out(h, t0)) return LAP_ERR_TIMEOUT;
+    }
+}
+
+// FP64 preconditioned CG on the centred right-hand side h.bs (tree order).
+lap_status cg_fp64(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
+{
+    const cudaStream_t s = h.s;
+    const auto &w = h.w64;
+    const auto &st = h.st64;
+    const int64_t n = h.M64.off[1];
+    const lap_options &o = h.m.opt;
+    k_cg_reset<<<1, 1, 0, s>>>(st.sc, o.tol, o.maxit, is_pegp(h) ? 1 : 0);
+    k_center_init<double><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), h.bs, w.r, w.x, st.sc,
+                                                            st.part, st.ticket);
+    CgScalars sc;
+    LAP_TRY(poll(h, st, sc));
+    if (!(sc.bnorm > 0.0)) {
+        info.relres = 0.0;
+        return LAP_OK;
+    }
+    int inner = 0;
+    LAP_TRY(apply_precond<double>(h, false, t0, inner));
+    pupdate<double>(h, n, is_plain(h) ? w.r : w.z, w.p, st, s);
+    lap_status result = LAP_ERR_NO_CONVERGENCE;
+    for (;;) {
+        lap_status it = iterate<double>(h, t0, inner, sc);
+        if (it != LAP_OK) {
+            result = it;
+            break;
+        }
+        info.relres_recurrence = sc.relres;
+        if (sc.flag == kConverged) {
+            // confirm with the true residual r = Pi b - L x
+            spmv<double, 1>(h, h.L64, h.tpr, w.x, nullptr, h.bs, w.r, st, s);
+            LAP_TRY(poll(h, st, sc));
+            if (sc.relres <= o.tol) {
+                result = LAP_OK;
+                break;
+            }
+            if (sc.iter >= o.maxit || info.restarts >= 8) break;
+            info.restarts += 1;
+            k_cg_restart<<<1, 1, 0, s>>>(st.sc);
+            LAP_TRY(apply_precond<double>(h, false, t0, inner));
+            pupdate<double>(h, n, is_plain(h) ? w.r : w.z, w.p, st, s);
+            continue;
+        }
+        result = sc.flag == kBreakdown ? LAP_ERR_BREAKDOWN : LAP_ERR_NO_CONVERGENCE;
+        break;
+    }
+    if (result != LAP_OK) {
+        spmv<double, 1>(h, h.L64, h.tpr, w.x, nullptr, h.bs, w.r, st, s);
+        CgScalars tmp;
+        LAP_TRY(poll(h, st, tmp));
+        sc.relres = tmp.relres;
+    }
+    info.iterations = sc.iter;
+    info.inner_iterations = inner;
+    info.relres = sc.relres;
+    return result;
+}
+
+// Mixed precision: FP64 residual refresh + FP32 inner CG per refinement step.
+lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
+{
+    const cudaStream_t s = h.s;
+    const int64_t n = h.M64.off[1];
+    const int ni = static_cast<int>(n);
+    const lap_options &o = h.m.opt;
+    const CgState &so = h.st64;
+    const CgState &si = h.st32;
+    k_cg_reset<<<1, 1, 0, s>>>(so.sc, o.tol, o.maxit, 0);
+    k_center_init<double><<<grid_for(h, n), kBlock, 0, s>>>(ni, h.bs, h.w64.r, h.w64.x, so.sc, so.part,
+                                                            so.ticket);
+    CgScalars sc;
+    LAP_TRY(poll(h, so, sc));
+    if (!(sc.bnorm > 0.0)) {
+        info.relres = 0.0;
+        return LAP_OK;
+    }
+    double relres = 1.0;
+    int total = 0, inner = 0;
+    lap_status result = LAP_ERR_NO_CONVERGENCE;
+    for (int ref = 0;; ++ref) {
+        if (ref > 0) {
+            spmv<double, 1>(h, h.L64, h.tpr, h.w64.x, nullptr, h.bs, h.w64.r, so, s);
+            LAP_TRY(poll(h, so, sc));
+            relres = sc.relres;
+            info.refinements = ref;
+            if (relres <= o.tol) {
+                result = LAP_OK;
+                break;
+            }
+            if (!std::isfinite(relres)) {
+                result = LAP_ERR_BREAKDOWN;
+                break;
+            }
+        }
+        if (ref >= o.max_refine || total >= o.maxit) break;
+        if (timed_out(h, t0)) {
+            result = LAP_ERR_TIMEOUT;
+            break;
+        }
+        const double tol_in = std::min(0.5, std::max(o.refine_tol, 0.3 * o.tol / relres));
+        k_cg_reset<<<1, 1, 0, s>>>(si.sc, tol_in, o.maxit - total, is_pegp(h) ? 1 : 0);
+        k_gather_sum<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, nullptr, h.w64.r, h.w32.r, si.sc,
+                                                             si.part, si.ticket);
+        k_center_init<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, h.w64.r, h.w32.r, h.w32.x, si.sc,
+                                                              si.part, si.ticket);
+        LAP_TRY(apply_precond<float>(h, false, t0, inner));
+        pupdate<float>(h, n, is_plain(h) ? h.w32.r : h.w32.z, h.w32.p, si, s);
+        CgScalars sci;
+        lap_status it = iterate<float>(h, t0, inner, sci);
+        if (it != LAP_OK) {
+            result = it;
+            break;
+        }
+        total += sci.iter;
+        k_add_correction<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, h.w64.x, h.w32.x);
+        info.relres_recurrence = sci.relres;
+        if (sci.flag == kBreakdown && sci.iter == 0) {
+            result = LAP_ERR_BREAKDOWN;
+            break;
+        }
+    }
+    if (result != LAP_OK && result != LAP_ERR_BREAKDOWN) {
+        spmv<double, 1>(h, h.L64, h.tpr, h.w64.x, nullptr, h.bs, h.w64.r, so, s);
+        LAP_TRY(poll(h, so, sc));
+        relres = sc.relres;
+    }
+    info.iterations = total;
+    info.inner_iterations = inner;
+    info.relres = relres;
+    return result;
+}
+
+// caller stream -> private stream ordering
+lap_status enter(lap_handle_s &h, cudaStream_t user)
+{
+    LAP_CK(cudaSetDevice(h.device));
+    LAP_CK(cudaEventRecord(h.ev_in, user));
+    LAP_CK(cudaStreamWaitEvent(h.s, h.ev_in, 0));
+    return LAP_OK;
+}
+
+lap_status leave(lap_handle_s &h, cudaStream_t user)
+{
+    LAP_CK(cudaEventRecord(h.ev_out, h.s));
+    LAP_CK(cudaStreamWaitEvent(user, h.ev_out, 0));
+    LAP_CK(cudaGetLastError());
+    return LAP_OK;
+}
+
+lap_status solve_core(lap_handle_s &h, const double *b, double *x, lap_solve_info &info)
+{
+    const auto t0 = Clock::now();
+    const cudaStream_t s = h.s;
+    const int n = static_cast<int>(h.M64.off[1]);
+    k_gather_sum<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.perm1, b, h.bs, h.st64.sc, h.st64.part,
+                                                          h.st64.ticket);
+    lap_status st = h.m.opt.precision == LAP_MIXED ? cg_mixed(h, t0, info) : cg_fp64(h, t0, info);
+    // x = Pi x back in the caller's numbering (also for a non-converged result)
+    k_mean<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.w64.x, h.stb.sc, h.stb.part, h.stb.ticket);
+    k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.perm1, h.w64.x, x,
+                                                             &h.stb.sc->tmp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return LAP_ERR_CUDA;
+    return st;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+lap_status upload_model(lap_handle_s &h, cudaStream_t user)
+{
+    (void)user;
+    const HostModel &m = h.m;
+    LAP_CK(cudaGetDevice(&h.device));
+    LAP_CK(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, h.device));
+    h.grid_cap = std::min(h.sms * 8, kMaxRedBlocks);
+    LAP_CK(cudaStreamCreateWithFlags(&h.s, cudaStreamNonBlocking));
+    LAP_CK(cudaEventCreateWithFlags(&h.ev_in, cudaEventDisableTiming));
+    LAP_CK(cudaEventCreateWithFlags(&h.ev_out, cudaEventDisableTiming));
+    LAP_CK(cudaMallocHost(&h.hsc, sizeof(CgScalars)));
+
+    const bool mixed = m.opt.precision == LAP_MIXED;
+    const int64_t n = m.lev[0].n, nt = m.offset[m.levels];
+    LAP_TRY(upload_csr<double>(h, m.L1, h.L64, nullptr));
+    if (mixed) LAP_TRY(upload_csr<float>(h, m.L1, h.L32, &h.L64));
+    LAP_TRY(upload_msp<double>(h, m, h.M64, nullptr));
+    if (mixed) LAP_TRY(upload_msp<float>(h, m, h.M32, &h.M64));
+    const double avg = static_cast<double>(m.L1.rp[n]) / static_cast<double>(n);
+    h.tpr = m.opt.spmv_tpr > 0 ? m.opt.spmv_tpr : auto_tpr(avg);
+    if (m.has_LH) {
+        LAP_TRY(upload_csr<double>(h, m.LH, h.H64, nullptr));
+        if (mixed) LAP_TRY(upload_csr<float>(h, m.LH, h.H32, &h.H64));
+        h.tprH = auto_tpr(static_cast<double>(m.LH.rp[m.LH.n]) / static_cast<double>(m.LH.n));
+    }
+    LAP_TRY(upload(h, &h.perm1, m.lev[0].perm));
+    {
+        std::vector<int64_t> xm(static_cast<size_t>(nt));
+        for (int k = 0; k < m.levels; ++k)
+            for (int64_t i = 0; i < m.lev[k].n; ++i) xm[m.offset[k] + i] = m.offset[k] + m.lev[k].perm[i];
+        LAP_TRY(upload(h, &h.xmap, xm));
+    }
+    h.bs = dalloc<double>(h, n);
+    if (!h.bs) return LAP_ERR_OOM;
+    LAP_TRY(alloc_vectors<double>(h, h.w64, n, nt, true, true));
+    if (mixed) LAP_TRY(alloc_vectors<float>(h, h.w32, n, nt, true, true));
+    if (m.has_LH) {
+        LAP_TRY(alloc_vectors<double>(h, h.e64, nt, nt, true, true));
+        if (mixed) LAP_TRY(alloc_vectors<float>(h, h.e32, nt, nt, true, true));
+    }
+    LAP_TRY(alloc_state(h, h.st64));
+    LAP_TRY(alloc_state(h, h.st32));
+    LAP_TRY(alloc_state(h, h.ste64));
+    LAP_TRY(alloc_state(h, h.ste32));
+    LAP_TRY(alloc_state(h, h.stb));
+    LAP_CK(cudaDeviceSynchronize());
+    return LAP_OK;
+}
+
+void destroy_handle(lap_handle_s &h)
+{
+    if (h.s) cudaStreamSynchronize(h.s);
+    for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    h.bufs.clear();
+    if (h.hsc) cudaFreeHost(h.hsc);
+    if (h.ev_in) cudaEventDestroy(h.ev_in);
+    if (h.ev_out) cudaEventDestroy(h.ev_out);
+    if (h.s) cudaStreamDestroy(h.s);
+    h.hsc = nullptr;
+    h.s = nullptr;
+}
+
+lap_status solve_device(lap_handle_s &h, const double *b, double *x, cudaStream_t user,
+                        lap_solve_info &info)
+{
+    LAP_TRY(enter(h, user));
+    const lap_status st = solve_core(h, b, x, info);
+    const lap_status st2 = leave(h, user);
+    LAP_CK(cudaStreamSynchronize(h.s));
+    return st != LAP_OK ? st : st2;
+}
+
+lap_status solve_host(lap_handle_s &h, const double *b, double *x, cudaStream_t user,
+                      lap_solve_info &info)
+{
+    const int64_t n = h.M64.off[1];
+    if (!h.bin) {
+        h.bin = dalloc<double>(h, n);
+        h.xout = dalloc<double>(h, n);
+        if (!h.bin || !h.xout) return LAP_ERR_OOM;
+    }
+    LAP_TRY(enter(h, user));
+    LAP_CK(cudaMemcpyAsync(h.bin, b, n * sizeof(double), cudaMemcpyHostToDevice, h.s));
+    const lap_status st = solve_core(h, h.bin, h.xout, info);
+    LAP_CK(cudaMemcpyAsync(x, h.xout, n * sizeof(double), cudaMemcpyDeviceToHost, h.s));
+    const lap_status st2 = leave(h, user);
+    LAP_CK(cudaStreamSynchronize(h.s));
+    return st != LAP_OK ? st : st2;
+}
+
+// ---------------------------------------------------------------------------
+// building blocks (FP64, device-resident)
+// ---------------------------------------------------------------------------
+lap_status block_laplacian(lap_handle_s &h, const double *x, double *y, cudaStream_t user)
+{
+    LAP_TRY(enter(h, user));
+    const int n = h.L64.n;
+    k_gather<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, x, h.w64.p);
+    spmv<double, 2>(h, h.L64, h.tpr, h.w64.p, h.w64.q, nullptr, nullptr, h.stb, h.s);
+    k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, h.w64.q, y, nullptr);
+    return leave(h, user);
+}
+
+lap_status block_precond(lap_handle_s &h, const double *r, double *z, cudaStream_t user)
+{
+    LAP_TRY(enter(h, user));
+    const int n = h.L64.n;
+    const CgState &st = h.st64;
+    k_gather_sum<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, r, h.bs, st.sc, st.part,
+                                                            st.ticket);
+    k_center_init<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.bs, h.w64.r, h.w64.x, st.sc, st.part,
+                                                             st.ticket);
+    k_cg_reset<<<1, 1, 0, h.s>>>(st.sc, 0.0, 1, is_pegp(h) ? 1 : 0);
+    int inner = 0;
+    LAP_TRY(apply_precond<double>(h, false, Clock::now(), inner));
+    k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, is_plain(h) ? h.w64.r : h.w64.z,
+                                                               z, &st.sc->zmean);
+    return leave(h, user);
+}
+
+lap_status block_restrict(lap_handle_s &h, const double *r, double *rt, cudaStream_t user)
+{
+    LAP_TRY(enter(h, user));
+    const int n = h.L64.n;
+    const int64_t nt = h.M64.off[h.M64.levels];
+    k_gather<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, r, h.w64.r);
+    restrict_tilde<double>(h, h.M64, h.w64.r, h.w64.Y, nullptr, h.w64.T, nullptr, h.s);
+    k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, h.w64.Y, rt, 1);
+    return leave(h, user);
+}
+
+lap_status block_prolong(lap_handle_s &h, const double *yt, double *z, cudaStream_t user)
+{
+    LAP_TRY(enter(h, user));
+    const int n = h.L64.n;
+    const int64_t nt = h.M64.off[h.M64.levels];
+    const auto &M = h.M64;
+    k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, yt, h.w64.Y, 0);
+    // Horner from the top: t_l = y_l, t_k = y_k - mu t_{k+1}(parent)
+    const int l = M.levels;
+    const int64_t ot = M.off[l - 1];
+    k_copy2<double><<<grid_for(h, M.ntop), kBlock, 0, h.s>>>(M.ntop, h.w64.Y + ot, h.w64.T + ot, nullptr,
+                                                            nullptr);
+    for (int k = l - 2; k >= 0; --k) {
+        const auto &Lk = M.lev[k];
+        k_msp_down<double><<<grid_for(h, Lk.nagg), kBlock, 0, h.s>>>(
+            Lk.nagg, Lk.seg, h.w64.Y + M.off[k], nullptr, h.w64.T + M.off[k + 1], nullptr,
+            h.w64.T + M.off[k], M.mu, nullptr);
+    }
+    k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, h.w64.T, z, nullptr);
+    return leave(h, user);
+}
+
+lap_status block_msp_solve(lap_handle_s &h, const double *rt, double *yt, cudaStream_t user)
+{
+    LAP_TRY(enter(h, user));
+    const int64_t nt = h.M64.off[h.M64.levels];
+    k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, rt, h.w64.A, 0);
+    msp_tilde<double>(h, h.M64, h.w64.A, h.w64.Y, nullptr, h.s);
+    k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, h.w64.Y, yt, 1);
+    return leave(h, user);
+}
+
+lap_status block_pegp(lap_handle_s &h, const double *xt, double *yt, cudaStream_t user)
+{
+    LAP_TRY(enter(h, user));
+    const int64_t nt = h.H64.n;
+    k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, xt, h.e64.p, 0);
+    spmv<double, 2>(h, h.H64, h.tprH, h.e64.p, h.e64.q, nullptr, nullptr, h.stb, h.s);
+    k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, h.e64.q, yt, 1);
+    return leave(h, user);
+}
+
+}  // namespace lap

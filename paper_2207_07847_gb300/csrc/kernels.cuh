@@ -1,0 +1,654 @@
+// Device kernels of the GB300 graph-Laplacian solver (sm_103a).
+//
+// Everything on this path is bound by HBM bandwidth or latency: CSR matvecs,
+// segmented sums and broadcasts over the aggregation tree, and vector updates
+// with dot products.  No kernel here is a dense contraction, so none uses the
+// tensor cores.  Vectors are stored in tree order (see lap_internal.h), which
+// makes every restriction/prolongation a pass over contiguous segments.
+//
+// V is the storage and arithmetic type of vectors, matrix values and sweeps
+// (double, or float for the mixed-precision inner solves); every reduction and
+// every CG scalar is accumulated and kept in double.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace lap {
+
+constexpr int kBlock = 256;
+constexpr int kMaxRedBlocks = 2048;   // capacity of the block-partials buffer
+constexpr int kRedSlots = 4;          // values reduced per kernel, at most
+
+// CG state kept on the device so that a whole iteration runs without the host.
+struct CgScalars {
+    double rho;        // r^T z (z projected)
+    double alpha;      // step length
+    double beta;       // direction update coefficient
+    double zmean;      // mean of the latest preconditioned residual
+    double pq;         // p^T L p
+    double qsum;       // sum of L p (zero up to rounding)
+    double rr, rs;     // ||r||^2 and sum(r) after the latest update
+    double bnorm;      // ||Pi b|| of the system being solved
+    double bmean;      // mean of b (projection)
+    double tol;        // recurrence tolerance on ||r|| / ||Pi b||
+    double relres;     // latest recurrence relative residual
+    double tmp;        // scratch sum
+    int iter;          // completed iterations
+    int maxit;
+    int flag;          // kRun, kConverged, kBreakdown, kMaxit
+    int flexible;      // 1: flexible (FCG) beta
+    int first;         // 1 while preparing the initial direction
+    int pad[3];
+};
+
+enum : int { kRun = 0, kConverged = 1, kBreakdown = 2, kMaxit = 3 };
+
+// ---------------------------------------------------------------------------
+// Deterministic grid reduction: every block reduces its NV partial sums, the
+// last block to finish (ticket) adds the per-block partials in block order.
+// All threads of every block must call it.  Returns true in the last block,
+// where tot[] holds the grid totals (valid in thread 0).
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV])
+{
+    __shared__ double sm[kBlock / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        v[i] = x;
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sm[wid][i] = v[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double x = lane < (int)(blockDim.x >> 5) ? sm[lane][i] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            v[i] = x;
+        }
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double *part, unsigned *ticket)
+{
+    __shared__ bool last;
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) part[blockIdx.x * NV + i] = v[i];
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += __ldcg(part + b * NV + i);
+        v[i] = x;
+    }
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+__device__ __forceinline__ bool halted(const CgScalars *sc) { return sc && sc->flag != kRun; }
+
+// ---------------------------------------------------------------------------
+// CSR Laplacian matvec  y = L x = diag .* x - A x  with TPR threads per row.
+// MODE 0: y = L x, reduce (x.y, sum y) and set alpha = rho / x.y
+// MODE 1: y(double) = bs - L x, reduce (||y||^2, sum y)   [true residual]
+// MODE 2: y = L x, no reduction
+// ---------------------------------------------------------------------------
+template <typename V, int TPR, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ w,
+       const V *__restrict__ dg, const V *__restrict__ x, V *__restrict__ y,
+       const double *__restrict__ bs, double *__restrict__ yres, CgScalars *sc, double *part,
+       unsigned *ticket)
+{
+    if (MODE != 2 && halted(sc)) return;
+    constexpr int RPW = 32 / TPR;      // rows per warp
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / TPR, l = lane % TPR;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    double a0 = 0.0, a1 = 0.0;
+    for (int r0 = gwarp * RPW; r0 < n; r0 += nwarp * RPW) {   // warp-uniform loop
+        const int row = r0 + sub;
+        const bool valid = row < n;
+        const int b = valid ? rp[row] : 0, e = valid ? rp[row + 1] : 0;
+        V s = V(0);
+        for (int p = b + l; p < e; p += TPR) s += w[p] * x[ci[p]];
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, TPR);
+        if (valid && l == 0) {
+            const V xi = x[row];
+            const V yi = dg[row] * xi - s;
+            if (MODE == 1) {
+                const double ri = bs[row] - (double)yi;
+                yres[row] = ri;
+                a0 += ri * ri;
+                a1 += ri;
+            } else {
+                y[row] = yi;
+                if (MODE == 0) {
+                    a0 += (double)xi * (double)yi;
+                    a1 += (double)yi;
+                }
+            }
+        }
+    }
+    if (MODE == 2) return;
+    double v[2] = {a0, a1};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        if (MODE == 0) {
+            sc->pq = v[0];
+            sc->qsum = v[1];
+            const double alpha = sc->rho / v[0];
+            if (!(v[0] > 0.0) || !isfinite(alpha)) sc->flag = kBreakdown;
+            sc->alpha = alpha;
+        } else {
+            sc->rr = v[0];
+            sc->rs = v[1];
+            sc->relres = sqrt(v[0]) / sc->bnorm;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused CG update + finest-level restriction and elimination (one thread per
+// level-2 aggregate, whose members are contiguous):
+//   UPDATE: x += alpha p, r -= alpha q                  (CG step)
+//   reduce ||r||^2, sum r                               (convergence test)
+//   SWEEP : a_1 = r; delta_1 = M_A^{-1} a_A per aggregate A  (Section 3.3)
+//           a_2(J) = gamma * sum_{u in J} a_1(u)        (restriction)
+// M_A = s L_intra(A) + pw diag(out): leftovers are eliminated onto the pair
+// (coefficients g_a, g_b, 1/d), the pair is solved with the inverse 2x2 Schur
+// complement, leftovers are back-substituted.  The finalise step tests
+// convergence and advances the iteration counter.
+// ---------------------------------------------------------------------------
+// PLAIN (no sweep): unpreconditioned CG, the finalise step also forms
+// rho = r^T Pi r and beta.  Without SWEEP, d1 (if not null) receives a copy of
+// the updated r (input of an in-place sweep that follows).
+template <typename V, bool UPDATE, bool SWEEP, bool PLAIN>
+__global__ void __launch_bounds__(kBlock)
+k_update_up1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
+             const V *__restrict__ lcf, V *__restrict__ x, V *__restrict__ r,
+             const V *__restrict__ p, const V *__restrict__ q, V *__restrict__ d1,
+             V *__restrict__ a2, V gamma, CgScalars *sc, double *part, unsigned *ticket)
+{
+    if (halted(sc)) return;
+    double rr = 0.0, rs = 0.0;
+    const V al = UPDATE ? (V)sc->alpha : V(0);
+    if (SWEEP) {
+        for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
+            const int b0 = seg[J], e = seg[J + 1];
+            V ra = r[b0], rb = r[b0 + 1];
+            if (UPDATE) {
+                x[b0] += al * p[b0];
+                x[b0 + 1] += al * p[b0 + 1];
+                ra -= al * q[b0];
+                rb -= al * q[b0 + 1];
+                r[b0] = ra;
+                r[b0 + 1] = rb;
+            }
+            rr += (double)ra * ra + (double)rb * rb;
+            rs += (double)ra + (double)rb;
+            V sum = ra + rb, ha = ra, hb = rb;
+            const V *lc = lcf + 3 * (b0 - 2 * J);
+            for (int t = b0 + 2; t < e; ++t) {
+                V rl = r[t];
+                if (UPDATE) {
+                    x[t] += al * p[t];
+                    rl -= al * q[t];
+                    r[t] = rl;
+                }
+                rr += (double)rl * rl;
+                rs += (double)rl;
+                sum += rl;
+                const V *c = lc + 3 * (t - b0 - 2);
+                ha += c[0] * rl;
+                hb += c[1] * rl;
+            }
+            const V i0 = inv[3 * J], i1 = inv[3 * J + 1], i2 = inv[3 * J + 2];
+            const V da = i0 * ha + i1 * hb, db = i1 * ha + i2 * hb;
+            d1[b0] = da;
+            d1[b0 + 1] = db;
+            for (int t = b0 + 2; t < e; ++t) {
+                const V *c = lc + 3 * (t - b0 - 2);
+                d1[t] = r[t] * c[2] + c[0] * da + c[1] * db;
+            }
+            a2[J] = gamma * sum;
+        }
+    } else {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            V ri = r[i];
+            if (UPDATE) {
+                x[i] += al * p[i];
+                ri -= al * q[i];
+                r[i] = ri;
+            }
+            if (d1) d1[i] = ri;
+            rr += (double)ri * ri;
+            rs += (double)ri;
+        }
+    }
+    double v[2] = {rr, rs};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        sc->rr = v[0];
+        sc->rs = v[1];
+        if (UPDATE) {
+            sc->iter += 1;
+            const double rel = sqrt(v[0]) / sc->bnorm;
+            sc->relres = rel;
+            if (!isfinite(rel)) sc->flag = kBreakdown;
+            else if (rel <= sc->tol) sc->flag = kConverged;
+            else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+        }
+        if (!SWEEP && PLAIN) {
+            // unpreconditioned CG: z = Pi r
+            const double m = v[1] / (double)n;
+            const double rho_new = v[0] - m * v[1];
+            sc->zmean = m;
+            sc->beta = sc->first ? 0.0 : rho_new / sc->rho;
+            sc->rho = rho_new;
+            sc->first = 0;
+        }
+    }
+}
+
+// Restriction + elimination on level k >= 2 (thread per level-(k+1) aggregate).
+// a holds a_k on entry and delta_k on exit; anext(J) = gamma*sum a_k + f_{k+1}(J).
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_msp_up(int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
+         const V *__restrict__ lcf, V *__restrict__ a, V *anext, V gamma,
+         const V *fnext, const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
+        const int b0 = seg[J], e = seg[J + 1];
+        const V aa = a[b0], ab = a[b0 + 1];
+        V sum = aa + ab, ha = aa, hb = ab;
+        const V *lc = lcf + 3 * (b0 - 2 * J);
+        for (int t = b0 + 2; t < e; ++t) {
+            const V al = a[t];
+            const V *c = lc + 3 * (t - b0 - 2);
+            sum += al;
+            ha += c[0] * al;
+            hb += c[1] * al;
+        }
+        const V i0 = inv[3 * J], i1 = inv[3 * J + 1], i2 = inv[3 * J + 2];
+        const V da = i0 * ha + i1 * hb, db = i1 * ha + i2 * hb;
+        for (int t = b0 + 2; t < e; ++t) {
+            const V *c = lc + 3 * (t - b0 - 2);
+            a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
+        }
+        a[b0] = da;
+        a[b0 + 1] = db;
+        V nx = gamma * sum;
+        if (fnext) nx += fnext[J];
+        anext[J] = nx;
+    }
+}
+
+// Top level: y = G a with G the dense pseudo-inverse (FP64), one warp per row.
+// Writes y to both the y- and t-arrays of the top level (t_l = y_l).
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_coarse(int m, const double *__restrict__ G, const V *__restrict__ a, V *__restrict__ y,
+         V *__restrict__ t, const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= m) return;
+    double s = 0.0;
+    for (int j = lane; j < m; j += 32) s += G[(size_t)row * m + j] * (double)a[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        y[row] = (V)s;
+        if (t) t[row] = (V)s;
+    }
+}
+
+// Prolongation / back-substitution on level k >= 2 (thread per level-(k+1)
+// aggregate J):  y_k(u) = y_{k+1}(J) + delta_k(u),  t_k(u) = y_k(u) - mu t_{k+1}(J).
+// With t == nullptr only y is produced (expanded-space MSP solve); with
+// yp == nullptr the parents' y are taken as zero, which turns the pass into
+// the Horner step t_k = delta_k - mu t_{k+1} of the prolongation P(mu).
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_msp_down(int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
+           const V *__restrict__ yp, const V *__restrict__ tp, V *__restrict__ y,
+           V *__restrict__ t, V mu, const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
+        const int b0 = seg[J], e = seg[J + 1];
+        const V yJ = yp ? yp[J] : V(0);
+        const V base = t ? yJ - mu * tp[J] : V(0);
+        for (int u = b0; u < e; ++u) {
+            const V d = delta[u];
+            if (y) y[u] = yJ + d;
+            if (t) t[u] = base + d;
+        }
+    }
+}
+
+// Restriction of one level: s_{k+1}(J) = sum_{u in J} s_k(u); the scaled value
+// coef * s_{k+1} goes to rt and (if given) to a.  Section 2.2: the level-k
+// block of P(mu)^T r is (-mu)^(k-1) (P^k)^T r.
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_restrict_level(int nagg, const int *__restrict__ seg, const V *__restrict__ s_in,
+                 V *__restrict__ s_out, V *__restrict__ rt, V *__restrict__ a, V coef,
+                 const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
+        V sum = V(0);
+        for (int u = seg[J]; u < seg[J + 1]; ++u) sum += s_in[u];
+        s_out[J] = sum;
+        const V v = coef * sum;
+        if (rt) rt[J] = v;
+        if (a) a[J] = v;
+    }
+}
+
+// out1 = out2 = in (either output may be null)
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_copy2(int64_t n, const V *__restrict__ in, V *__restrict__ o1, V *__restrict__ o2,
+        const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V v = in[i];
+        if (o1) o1[i] = v;
+        if (o2) o2[i] = v;
+    }
+}
+
+// Finest level of the prolongation, producing the preconditioned residual
+// z = t_1 and the reductions for the projection and the CG scalars:
+// sum z, r.z, z.q  ->  zmean, rho and beta (standard or flexible).
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_msp_down1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
+            const V *__restrict__ yp, const V *__restrict__ tp, const V *__restrict__ r,
+            const V *__restrict__ q, V *__restrict__ z, V mu, CgScalars *sc, double *part,
+            unsigned *ticket)
+{
+    if (halted(sc)) return;
+    double sz = 0.0, srz = 0.0, szq = 0.0;
+    const bool flex = sc->flexible && !sc->first;
+    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
+        const int b0 = seg[J], e = seg[J + 1];
+        const V base = (yp ? yp[J] : V(0)) - mu * tp[J];
+        for (int u = b0; u < e; ++u) {
+            const V zu = base + delta[u];
+            z[u] = zu;
+            sz += (double)zu;
+            srz += (double)r[u] * (double)zu;
+            if (flex) szq += (double)zu * (double)q[u];
+        }
+    }
+    double v[3] = {sz, srz, szq};
+    if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
+        const double m = v[0] / (double)n;
+        const double rho_new = v[1] - m * sc->rs;
+        sc->zmean = m;
+        if (sc->first) sc->beta = 0.0;
+        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
+        else sc->beta = rho_new / sc->rho;
+        sc->rho = rho_new;
+        sc->first = 0;
+        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+    }
+}
+
+// Single-level hierarchy: z = G r directly (dense pseudo-inverse), with the
+// same reductions as k_msp_down1.  One warp per row.
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_dense_z(int n, const double *__restrict__ G, const V *__restrict__ r, const V *__restrict__ q,
+          V *__restrict__ z, CgScalars *sc, double *part, unsigned *ticket)
+{
+    if (halted(sc)) return;
+    const int lane = threadIdx.x & 31;
+    const bool flex = sc->flexible && !sc->first;
+    double sz = 0.0, srz = 0.0, szq = 0.0;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+        double s = 0.0;
+        for (int j = lane; j < n; j += 32) s += G[(size_t)row * n + j] * (double)r[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const V zu = (V)s;
+            z[row] = zu;
+            sz += (double)zu;
+            srz += (double)r[row] * (double)zu;
+            if (flex) szq += (double)zu * (double)q[row];
+        }
+    }
+    double v[3] = {sz, srz, szq};
+    if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
+        const double m = v[0] / (double)n;
+        const double rho_new = v[1] - m * sc->rs;
+        sc->zmean = m;
+        if (sc->first) sc->beta = 0.0;
+        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
+        else sc->beta = rho_new / sc->rho;
+        sc->rho = rho_new;
+        sc->first = 0;
+        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+    }
+}
+
+// p = (z - zmean) + beta p
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_pupdate(int64_t n, const V *__restrict__ z, V *__restrict__ p, const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    const V m = (V)sc->zmean, be = (V)sc->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (z[i] - m) + be * p[i];
+}
+
+// ---------------------------------------------------------------------------
+// Permutation between the caller's numbering and tree order, projection.
+// ---------------------------------------------------------------------------
+// out[i] = (V) in[perm[i]], reduce sum -> sc->bmean = sum / n
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_gather_sum(int n, const int *__restrict__ perm, const double *__restrict__ in, V *__restrict__ out,
+             CgScalars *sc, double *part, unsigned *ticket)
+{
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = in[perm ? perm[i] : i];
+        out[i] = (V)v;
+        s += v;
+    }
+    double v[1] = {s};
+    if (grid_sum<1>(v, part, ticket) && threadIdx.x == 0) sc->bmean = v[0] / (double)n;
+}
+
+// b -= bmean (double, in place), r = (V) b, x = 0; reduce ||b||^2 and sum(r) ->
+// bnorm, rr, rs; converged at once when b projects to zero.
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_center_init(int n, double *__restrict__ b, V *__restrict__ r, V *__restrict__ x, CgScalars *sc,
+              double *part, unsigned *ticket)
+{
+    const double m = sc->bmean;
+    double s2 = 0.0, s1 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = b[i] - m;
+        b[i] = v;
+        const V rv = (V)v;
+        r[i] = rv;
+        if (x) x[i] = V(0);
+        s2 += (double)rv * (double)rv;
+        s1 += (double)rv;
+    }
+    double v[2] = {s2, s1};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        sc->bnorm = sqrt(v[0]);
+        sc->rr = v[0];
+        sc->rs = v[1];
+        sc->relres = 1.0;
+        sc->iter = 0;
+        sc->first = 1;
+        sc->flag = (v[0] > 0.0) ? kRun : kConverged;
+    }
+}
+
+// mean of x -> sc->tmp
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_mean(int n, const V *__restrict__ x, CgScalars *sc, double *part, unsigned *ticket)
+{
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += (double)x[i];
+    double v[1] = {s};
+    if (grid_sum<1>(v, part, ticket) && threadIdx.x == 0) sc->tmp = v[0] / (double)n;
+}
+
+// out[perm[i]] = x[i] - *shift  (back to the caller's numbering; shift may be null)
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_scatter_shift(int n, const int *__restrict__ perm, const V *__restrict__ x, double *__restrict__ out,
+                const double *shift)
+{
+    const double m = shift ? *shift : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[perm ? perm[i] : i] = (double)x[i] - m;
+}
+
+// out[i] = (V) in[perm[i]]
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_gather(int n, const int *__restrict__ perm, const double *__restrict__ in, V *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (V)in[perm ? perm[i] : i];
+}
+
+// x = 0; reduce ||r||^2, sum r -> bnorm, rr, rs; start a CG (expanded-space inner solve)
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_vec_init(int64_t n, const V *__restrict__ r, V *__restrict__ x, CgScalars *sc, double *part,
+           unsigned *ticket)
+{
+    double s2 = 0.0, s1 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)r[i];
+        x[i] = V(0);
+        s2 += v * v;
+        s1 += v;
+    }
+    double v[2] = {s2, s1};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        sc->bnorm = sqrt(v[0]);
+        sc->rr = v[0];
+        sc->rs = v[1];
+        sc->relres = 1.0;
+        sc->iter = 0;
+        sc->first = 1;
+        sc->flag = (v[0] > 0.0) ? kRun : kConverged;
+    }
+}
+
+// Reductions of a flat preconditioned residual z (expanded-space CG):
+// sum z, r.z -> zmean, rho, beta (standard CG).
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_zred(int64_t n, const V *__restrict__ z, const V *__restrict__ r, CgScalars *sc, double *part,
+       unsigned *ticket)
+{
+    if (halted(sc)) return;
+    double sz = 0.0, srz = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double zu = (double)z[i];
+        sz += zu;
+        srz += (double)r[i] * zu;
+    }
+    double v[2] = {sz, srz};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        const double m = v[0] / (double)n;
+        const double rho_new = v[1] - m * sc->rs;
+        sc->zmean = m;
+        sc->beta = sc->first ? 0.0 : rho_new / sc->rho;
+        sc->rho = rho_new;
+        sc->first = 0;
+        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+    }
+}
+
+// CG bookkeeping written from the host side of the stream.
+static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flexible)
+{
+    sc->tol = tol;
+    sc->maxit = maxit;
+    sc->flexible = flexible;
+    sc->iter = 0;
+    sc->flag = kRun;
+    sc->first = 1;
+}
+
+static __global__ void k_cg_restart(CgScalars *sc)
+{
+    sc->flag = kRun;
+    sc->first = 1;
+}
+
+// x64 += (double) d  (iterative refinement correction)
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_add_correction(int n, double *__restrict__ x, const V *__restrict__ d)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+// out[i] = (VO) in[i]
+template <typename VI, typename VO>
+__global__ void __launch_bounds__(kBlock)
+k_convert(int64_t n, const VI *__restrict__ in, VO *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (VO)in[i];
+}
+
+// plain gather/scatter by a permutation (expanded-space building blocks)
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_permute(int64_t n, const int64_t *__restrict__ idx, const V *__restrict__ in, V *__restrict__ out,
+          int scatter)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (scatter) out[idx[i]] = in[i];
+        else out[i] = in[idx[i]];
+    }
+}
+
+}  // namespace lap

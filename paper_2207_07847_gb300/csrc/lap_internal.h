@@ -1,0 +1,88 @@
+// Internal declarations of the GB300 graph-Laplacian solver library.
+// Host setup (setup.cpp) builds a HostModel; the CUDA side (solve.cu) uploads
+// it into a DeviceModel and runs the preconditioned CG kernels (kernels.cuh).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lap.h"
+
+namespace lap {
+
+// ---------------------------------------------------------------------------
+// Host-side model produced by the setup stage.
+//
+// Every level is stored in "tree order": the members of each aggregate are
+// contiguous (matched pair first, then leftovers by increasing id) and the
+// aggregates of level k appear in the tree order of level k+1.  Consequently
+// the subtree of any vertex is contiguous on every finer level, restriction is
+// a segmented sum over contiguous segments and prolongation a segmented
+// broadcast.  The top level keeps its own numbering.
+// ---------------------------------------------------------------------------
+struct HostLevel {
+    int64_t n = 0;
+    // adjacency in the hierarchy's own numbering (level 1: the input order)
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> w;
+    std::vector<double> deg;      // weighted degree d_k
+    // aggregation to level k+1 (empty on the top level)
+    std::vector<int32_t> agg;     // agg_k(u), hierarchy numbering
+    std::vector<int32_t> pa, pb;  // matched pair that created each aggregate
+    std::vector<double> out;      // out_k(u): weight from u to other aggregates
+    // tree order
+    std::vector<int32_t> perm;    // storage position -> hierarchy id
+    std::vector<int32_t> pos;     // hierarchy id -> storage position
+};
+
+struct HostCsr {                  // square CSR, off-diagonal entries + diagonal
+    int64_t n = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> w;        // positive edge weights (matrix entry is -w)
+    std::vector<double> diag;     // row sums of w
+};
+
+struct HostMspLevel {             // elimination data of level k < l (tree order)
+    int64_t n = 0, nagg = 0;
+    std::vector<int32_t> seg;     // [nagg+1] member ranges in level-k storage
+    std::vector<double> inv;      // [3*nagg] inverse 2x2 Schur complement (aa, ab, bb)
+    std::vector<double> lcf;      // [3*(n-2*nagg)] leftover (g_a, g_b, 1/d)
+};
+
+struct HostModel {
+    lap_options opt{};
+    double mu = 0.8;
+    int levels = 0;
+    std::vector<HostLevel> lev;
+    std::vector<int64_t> offset;  // expanded offsets, offset[k] = n_1 + .. + n_k
+    HostCsr L1;                   // level-1 Laplacian in tree order
+    std::vector<HostMspLevel> msp;
+    std::vector<double> coarse_pinv;   // dense (mu^(2(l-1)) L_l)^+ , n_l x n_l row-major
+    std::vector<double> c;        // c_k = sum_{i<k} (-mu)^i, k = 1..l (index k-1)
+    HostCsr LH;                   // L_H over the expanded vertices in tree order (PEGP)
+    bool has_LH = false;
+    int64_t edges_T = 0;
+};
+
+lap_status validate_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
+                        std::string *why);
+lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
+                       const lap_options &opt, HostModel &m);
+// edges of H (which = 0) or T (which = 1) in the hierarchy's expanded numbering, i < j
+void expanded_edges(const HostModel &m, int which, std::vector<int64_t> &I,
+                    std::vector<int64_t> &J, std::vector<double> &W);
+
+// splitmix64 output i (>= 1) for `seed` (Steele, Lea & Flood 2014)
+uint64_t splitmix64(uint64_t seed, uint64_t i);
+
+// ---------------------------------------------------------------------------
+// Device allocation through an optional caller allocator.
+// ---------------------------------------------------------------------------
+void *dev_alloc(size_t bytes, void *stream);
+void dev_free(void *p, void *stream);
+
+}  // namespace lap

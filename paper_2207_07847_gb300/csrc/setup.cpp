@@ -1,0 +1,596 @@
+// Host setup of the solver: input validation, the aggregation hierarchy
+// (Section 2.2), the tree-ordered storage layout, the elimination data of the
+// multilevel sparsifier T (Section 3.3), the top-level pseudo-inverse and, for
+// PEGP, the Laplacian of the positively weighted expanded graph H (Section 3.2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <utility>
+
+#include "lap_internal.h"
+
+namespace lap {
+
+uint64_t splitmix64(uint64_t seed, uint64_t i)
+{
+    // Steele, Lea & Flood (2014): state advances by the golden gamma, output
+    // is the variant-13 finaliser of the state.
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+lap_status validate_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
+                        std::string *why)
+{
+    auto fail = [&](lap_status s, const char *msg) {
+        if (why) *why = msg;
+        return s;
+    };
+    if (n < 2 || !rp || !ci || !w) return fail(LAP_ERR_INVALID_ARG, "n < 2 or null array");
+    if (n >= (int64_t(1) << 31) - 1) return fail(LAP_ERR_UNSUPPORTED, "n >= 2^31");
+    if (rp[0] != 0) return fail(LAP_ERR_INVALID_ARG, "row_ptr[0] != 0");
+    for (int64_t u = 0; u < n; ++u)
+        if (rp[u + 1] < rp[u]) return fail(LAP_ERR_INVALID_ARG, "row_ptr decreasing");
+    const int64_t nnz = rp[n];
+    if (nnz >= (int64_t(1) << 31)) return fail(LAP_ERR_UNSUPPORTED, "nnz >= 2^31");
+    for (int64_t u = 0; u < n; ++u) {
+        for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+            const int64_t v = ci[p];
+            if (v < 0 || v >= n) return fail(LAP_ERR_INVALID_ARG, "column out of range");
+            if (v == u) return fail(LAP_ERR_INVALID_ARG, "self-loop");
+            if (!(w[p] > 0.0) || !std::isfinite(w[p]))
+                return fail(LAP_ERR_BAD_WEIGHT, "weight not positive and finite");
+        }
+    }
+    // sorted copy of every row: duplicates and symmetry
+    std::vector<std::pair<int32_t, double>> s(static_cast<size_t>(nnz));
+    for (int64_t p = 0; p < nnz; ++p) s[p] = {ci[p], w[p]};
+    for (int64_t u = 0; u < n; ++u) {
+        auto b = s.begin() + rp[u], e = s.begin() + rp[u + 1];
+        std::sort(b, e, [](const auto &x, const auto &y) { return x.first < y.first; });
+        for (auto it = b; it + 1 < e; ++it)
+            if (it->first == (it + 1)->first)
+                return fail(LAP_ERR_INVALID_ARG, "duplicate entry");
+    }
+    for (int64_t u = 0; u < n; ++u) {
+        for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+            const int32_t v = s[p].first;
+            auto b = s.begin() + rp[v], e = s.begin() + rp[v + 1];
+            auto it = std::lower_bound(b, e, static_cast<int32_t>(u),
+                                       [](const auto &x, int32_t key) { return x.first < key; });
+            if (it == e || it->first != u || it->second != s[p].second)
+                return fail(LAP_ERR_NOT_SYMMETRIC, "matrix not symmetric");
+        }
+    }
+    // connectivity by breadth-first search
+    std::vector<char> seen(static_cast<size_t>(n), 0);
+    std::vector<int32_t> queue;
+    queue.reserve(static_cast<size_t>(n));
+    queue.push_back(0);
+    seen[0] = 1;
+    for (size_t h = 0; h < queue.size(); ++h) {
+        const int32_t u = queue[h];
+        for (int64_t p = rp[u]; p < rp[u + 1]; ++p)
+            if (!seen[ci[p]]) {
+                seen[ci[p]] = 1;
+                queue.push_back(ci[p]);
+            }
+    }
+    if (static_cast<int64_t>(queue.size()) != n)
+        return fail(LAP_ERR_NOT_CONNECTED, "graph not connected");
+    return LAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// aggregation hierarchy (Section 2.2)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Heaviest neighbour of u among those accepted by `eligible`; ties go to the
+// smaller id.  Returns -1 when no neighbour is eligible.
+template <class Pred>
+int32_t heaviest_neighbour(const HostLevel &L, int64_t u, Pred eligible)
+{
+    int32_t best = -1;
+    double best_w = 0.0;
+    for (int64_t p = L.rp[u]; p < L.rp[u + 1]; ++p) {
+        const int32_t v = L.ci[p];
+        if (!eligible(v)) continue;
+        const double wv = L.w[p];
+        if (best < 0 || wv > best_w || (wv == best_w && v < best)) {
+            best = v;
+            best_w = wv;
+        }
+    }
+    return best;
+}
+
+// Random-order maximal-weight matching of one level; level is 1-based.
+int64_t aggregate_level(HostLevel &L, uint64_t seed, int level, bool randomise)
+{
+    const int64_t n = L.n;
+    std::vector<int32_t> visit(static_cast<size_t>(n));
+    if (randomise) {
+        std::vector<std::pair<uint64_t, int32_t>> key(static_cast<size_t>(n));
+        const uint64_t hi = static_cast<uint64_t>(static_cast<uint32_t>(level)) << 32;
+        for (int64_t u = 0; u < n; ++u)
+            key[u] = {splitmix64(seed, (hi | static_cast<uint64_t>(u)) + 1), static_cast<int32_t>(u)};
+        std::sort(key.begin(), key.end());
+        for (int64_t i = 0; i < n; ++i) visit[i] = key[i].second;
+    } else {
+        std::iota(visit.begin(), visit.end(), 0);
+    }
+    L.agg.assign(static_cast<size_t>(n), -1);
+    L.pa.clear();
+    L.pb.clear();
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t u = visit[i];
+        if (L.agg[u] >= 0) continue;
+        const int32_t v = heaviest_neighbour(L, u, [&](int32_t x) { return L.agg[x] < 0; });
+        if (v < 0) continue;                         // leftover, handled below
+        const int32_t id = static_cast<int32_t>(L.pa.size());
+        L.agg[u] = L.agg[v] = id;
+        L.pa.push_back(u);
+        L.pb.push_back(v);
+    }
+    const int64_t nagg = static_cast<int64_t>(L.pa.size());
+    // A leftover saw only aggregated neighbours when it was visited and no later
+    // pair can have used it, so its heaviest neighbour is always a matched vertex.
+    for (int64_t u = 0; u < n; ++u) {
+        if (L.agg[u] >= 0) continue;
+        const int32_t v = heaviest_neighbour(L, u, [](int32_t) { return true; });
+        L.agg[u] = L.agg[v];
+    }
+    return nagg;
+}
+
+// Galerkin coarse graph: weight(I, J) = sum of fine weights between the two
+// aggregates, accumulated fine vertex by fine vertex in increasing id and CSR
+// position; coarse rows have sorted columns.
+void coarse_graph(const HostLevel &F, int64_t nc, HostLevel &C)
+{
+    const int64_t n = F.n;
+    std::vector<int64_t> start(static_cast<size_t>(nc) + 1, 0);
+    for (int64_t u = 0; u < n; ++u) ++start[F.agg[u] + 1];
+    std::partial_sum(start.begin(), start.end(), start.begin());
+    std::vector<int32_t> members(static_cast<size_t>(n));
+    {
+        std::vector<int64_t> cursor(start.begin(), start.end() - 1);
+        for (int64_t u = 0; u < n; ++u) members[cursor[F.agg[u]]++] = static_cast<int32_t>(u);
+    }
+    C.n = nc;
+    C.rp.assign(static_cast<size_t>(nc) + 1, 0);
+    C.ci.clear();
+    C.w.clear();
+    std::vector<double> acc(static_cast<size_t>(nc), 0.0);
+    std::vector<int32_t> stamp(static_cast<size_t>(nc), -1);
+    std::vector<int32_t> cols;
+    for (int64_t I = 0; I < nc; ++I) {
+        cols.clear();
+        for (int64_t t = start[I]; t < start[I + 1]; ++t) {
+            const int32_t u = members[t];
+            for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) {
+                const int32_t J = F.agg[F.ci[p]];
+                if (J == I) continue;
+                if (stamp[J] != I) {
+                    stamp[J] = static_cast<int32_t>(I);
+                    acc[J] = 0.0;
+                    cols.push_back(J);
+                }
+                acc[J] += F.w[p];
+            }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int32_t J : cols) {
+            C.ci.push_back(J);
+            C.w.push_back(acc[J]);
+        }
+        C.rp[I + 1] = static_cast<int64_t>(C.ci.size());
+    }
+}
+
+void degrees(HostLevel &L)
+{
+    L.deg.assign(static_cast<size_t>(L.n), 0.0);
+    for (int64_t u = 0; u < L.n; ++u) {
+        double d = 0.0;
+        for (int64_t p = L.rp[u]; p < L.rp[u + 1]; ++p) d += L.w[p];
+        L.deg[u] = d;
+    }
+}
+
+double edge_weight(const HostLevel &L, int64_t u, int64_t v)
+{
+    for (int64_t p = L.rp[u]; p < L.rp[u + 1]; ++p)
+        if (L.ci[p] == v) return L.w[p];
+    return 0.0;
+}
+
+// Dense inverse of an SPD matrix by Cholesky (row-major, in place -> out).
+bool spd_inverse(std::vector<double> &A, int64_t m)
+{
+    // A = R^T R with R upper triangular stored in the upper triangle
+    for (int64_t j = 0; j < m; ++j) {
+        double d = A[j * m + j];
+        for (int64_t k = 0; k < j; ++k) d -= A[k * m + j] * A[k * m + j];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        A[j * m + j] = d;
+        for (int64_t i = j + 1; i < m; ++i) {
+            double s = A[j * m + i];
+            for (int64_t k = 0; k < j; ++k) s -= A[k * m + j] * A[k * m + i];
+            A[j * m + i] = s / d;
+        }
+    }
+    // inverse of R (upper triangular) into Ri
+    std::vector<double> Ri(static_cast<size_t>(m * m), 0.0);
+    for (int64_t j = 0; j < m; ++j) {
+        Ri[j * m + j] = 1.0 / A[j * m + j];
+        for (int64_t i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int64_t k = i + 1; k <= j; ++k) s += A[i * m + k] * Ri[k * m + j];
+            Ri[i * m + j] = -s / A[i * m + i];
+        }
+    }
+    // A^{-1} = Ri Ri^T
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int64_t k = std::max(i, j); k < m; ++k) s += Ri[i * m + k] * Ri[j * m + k];
+            A[i * m + j] = s;
+        }
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// PEGP: Laplacian of H, the positive part of P(mu)^T L P(mu) (Section 3.2).
+//
+// For u on level k and J on level j >= k the entry of L_Gt is
+// (-mu)^(k+j-2) (L_k Pi_{k->j})(u, J), Pi the 0/1 map to level-j ancestors.
+// That entry is -W_k(u,J) for a non-ancestor J (W = weight from u into J's
+// level-k descendants) and out_{k->j}(u) for u's own ancestor (weight leaving
+// that ancestor's subtree).  The edge weight is minus the entry, so H keeps
+// all same-level edges, the ancestor edges at odd level distance with
+// out > 0, and the non-ancestor edges at even distance.  On two levels this
+// is the rule stated for the worked example of Section 3.1.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct EdgeAcc {
+    std::vector<int64_t> i, j;
+    std::vector<double> w;
+};
+
+void build_pegp(HostModel &m)
+{
+    const int l = m.levels;
+    const double mu = m.mu;
+    std::vector<double> mpow(static_cast<size_t>(2 * l + 2), 1.0);
+    for (size_t t = 1; t < mpow.size(); ++t) mpow[t] = mpow[t - 1] * mu;
+    // expanded index in tree order
+    auto xidx = [&](int k, int64_t u) { return m.offset[k] + m.lev[k].pos[u]; };
+
+    EdgeAcc E;
+    std::vector<int32_t> anc_u;     // ancestor chain scratch
+    std::vector<int32_t> nbr_anc;   // current ancestor of each neighbour
+    std::vector<double> nbr_w;
+    std::vector<std::pair<int32_t, double>> grp;
+    for (int k = 0; k < l; ++k) {
+        const HostLevel &L = m.lev[k];
+        for (int64_t u = 0; u < L.n; ++u) {
+            const int64_t deg = L.rp[u + 1] - L.rp[u];
+            nbr_anc.resize(static_cast<size_t>(deg));
+            nbr_w.resize(static_cast<size_t>(deg));
+            for (int64_t t = 0; t < deg; ++t) {
+                nbr_anc[t] = L.ci[L.rp[u] + t];
+                nbr_w[t] = L.w[L.rp[u] + t];
+                // same-level edge (k, k): weight mu^(2k) w; store once (u < v)
+                if (nbr_anc[t] > u)
+                    E.i.push_back(xidx(k, u)), E.j.push_back(xidx(k, nbr_anc[t])),
+                        E.w.push_back(mpow[2 * k] * nbr_w[t]);
+            }
+            int32_t a = static_cast<int32_t>(u);
+            for (int j = k + 1; j < l; ++j) {
+                const std::vector<int32_t> &up = m.lev[j - 1].agg;
+                a = up[a];
+                for (int64_t t = 0; t < deg; ++t) nbr_anc[t] = up[nbr_anc[t]];
+                const double scale = mpow[k + j];
+                if ((j - k) % 2 == 1) {
+                    double out = 0.0;
+                    for (int64_t t = 0; t < deg; ++t)
+                        if (nbr_anc[t] != a) out += nbr_w[t];
+                    if (out > 0.0)
+                        E.i.push_back(xidx(k, u)), E.j.push_back(xidx(j, a)),
+                            E.w.push_back(scale * out);
+                } else {
+                    grp.clear();
+                    for (int64_t t = 0; t < deg; ++t)
+                        if (nbr_anc[t] != a) grp.push_back({nbr_anc[t], nbr_w[t]});
+                    std::stable_sort(grp.begin(), grp.end(),
+                                     [](const auto &x, const auto &y) { return x.first < y.first; });
+                    for (size_t s = 0; s < grp.size();) {
+                        size_t e = s;
+                        double W = 0.0;
+                        while (e < grp.size() && grp[e].first == grp[s].first) W += grp[e++].second;
+                        E.i.push_back(xidx(k, u)), E.j.push_back(xidx(j, grp[s].first)),
+                            E.w.push_back(scale * W);
+                        s = e;
+                    }
+                }
+            }
+        }
+    }
+    // symmetric CSR over the expanded vertices (tree order), sorted columns
+    const int64_t nt = m.offset[l];
+    HostCsr &H = m.LH;
+    H.n = nt;
+    H.rp.assign(static_cast<size_t>(nt) + 1, 0);
+    for (size_t e = 0; e < E.i.size(); ++e) ++H.rp[E.i[e] + 1], ++H.rp[E.j[e] + 1];
+    std::partial_sum(H.rp.begin(), H.rp.end(), H.rp.begin());
+    H.ci.assign(static_cast<size_t>(H.rp[nt]), 0);
+    H.w.assign(static_cast<size_t>(H.rp[nt]), 0.0);
+    std::vector<int64_t> cur(H.rp.begin(), H.rp.end() - 1);
+    for (size_t e = 0; e < E.i.size(); ++e) {
+        H.ci[cur[E.i[e]]] = static_cast<int32_t>(E.j[e]);
+        H.w[cur[E.i[e]]++] = E.w[e];
+        H.ci[cur[E.j[e]]] = static_cast<int32_t>(E.i[e]);
+        H.w[cur[E.j[e]]++] = E.w[e];
+    }
+    H.diag.assign(static_cast<size_t>(nt), 0.0);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t r = 0; r < nt; ++r) {
+        row.clear();
+        for (int64_t p = H.rp[r]; p < H.rp[r + 1]; ++p) row.push_back({H.ci[p], H.w[p]});
+        std::sort(row.begin(), row.end());
+        double d = 0.0;
+        for (size_t t = 0; t < row.size(); ++t) {
+            H.ci[H.rp[r] + t] = row[t].first;
+            H.w[H.rp[r] + t] = row[t].second;
+            d += row[t].second;
+        }
+        H.diag[r] = d;
+    }
+    m.has_LH = true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
+                       const lap_options &opt, HostModel &m)
+{
+    m.opt = opt;
+    m.mu = opt.mu > 0.0 ? opt.mu : 1.0 / std::sqrt(static_cast<double>(n));
+    if (!(m.mu > 0.0 && m.mu < 1.0)) return LAP_ERR_INVALID_ARG;
+    if (opt.coarse_max < 1 || opt.max_levels < 0) return LAP_ERR_INVALID_ARG;
+
+    m.lev.clear();
+    m.lev.emplace_back();
+    {
+        HostLevel &L = m.lev.back();
+        L.n = n;
+        L.rp.assign(rp, rp + n + 1);
+        L.ci.assign(ci, ci + rp[n]);
+        L.w.assign(w, w + rp[n]);
+        degrees(L);
+    }
+    for (int k = 1;; ++k) {
+        HostLevel &F = m.lev.back();
+        if (F.n <= opt.coarse_max) break;
+        if (opt.max_levels && k >= opt.max_levels) break;
+        if (k >= LAP_MAX_LEVELS) break;
+        const int64_t nc = aggregate_level(F, opt.seed, k, opt.order_random != 0);
+        if (nc < 2) {
+            F.agg.clear();
+            F.pa.clear();
+            F.pb.clear();
+            break;
+        }
+        HostLevel C;
+        coarse_graph(F, nc, C);
+        degrees(C);
+        // weight from each vertex to other aggregates (no cancellation)
+        F.out.assign(static_cast<size_t>(F.n), 0.0);
+        for (int64_t u = 0; u < F.n; ++u) {
+            double o = 0.0;
+            for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p)
+                if (F.agg[F.ci[p]] != F.agg[u]) o += F.w[p];
+            F.out[u] = o;
+        }
+        m.lev.push_back(std::move(C));
+    }
+    const int l = static_cast<int>(m.lev.size());
+    m.levels = l;
+    m.offset.assign(static_cast<size_t>(l) + 1, 0);
+    for (int k = 0; k < l; ++k) m.offset[k + 1] = m.offset[k] + m.lev[k].n;
+    m.c.assign(static_cast<size_t>(l), 1.0);
+    for (int k = 1; k < l; ++k) m.c[k] = m.c[k - 1] + std::pow(-m.mu, k);
+
+    // ---- tree order, top level down -------------------------------------
+    {
+        HostLevel &T = m.lev[l - 1];
+        T.perm.resize(static_cast<size_t>(T.n));
+        std::iota(T.perm.begin(), T.perm.end(), 0);
+        T.pos = T.perm;
+    }
+    m.msp.assign(static_cast<size_t>(l > 1 ? l - 1 : 0), HostMspLevel{});
+    for (int k = l - 2; k >= 0; --k) {
+        HostLevel &F = m.lev[k];
+        const HostLevel &C = m.lev[k + 1];
+        const int64_t nagg = C.n;
+        // leftovers of each aggregate in increasing id
+        std::vector<int64_t> lstart(static_cast<size_t>(nagg) + 1, 0);
+        std::vector<char> paired(static_cast<size_t>(F.n), 0);
+        for (int64_t J = 0; J < nagg; ++J) paired[F.pa[J]] = paired[F.pb[J]] = 1;
+        for (int64_t u = 0; u < F.n; ++u)
+            if (!paired[u]) ++lstart[F.agg[u] + 1];
+        std::partial_sum(lstart.begin(), lstart.end(), lstart.begin());
+        std::vector<int32_t> left(static_cast<size_t>(lstart[nagg]));
+        {
+            std::vector<int64_t> cur(lstart.begin(), lstart.end() - 1);
+            for (int64_t u = 0; u < F.n; ++u)
+                if (!paired[u]) left[cur[F.agg[u]]++] = static_cast<int32_t>(u);
+        }
+        HostMspLevel &S = m.msp[k];
+        S.n = F.n;
+        S.nagg = nagg;
+        S.seg.assign(static_cast<size_t>(nagg) + 1, 0);
+        S.inv.assign(static_cast<size_t>(3 * nagg), 0.0);
+        S.lcf.assign(static_cast<size_t>(3 * (F.n - 2 * nagg)), 0.0);
+        F.perm.clear();
+        F.perm.reserve(static_cast<size_t>(F.n));
+        const double s = std::pow(m.mu, 2 * k);        // level scaling mu^(2(k-1)), 1-based
+        const double pw = std::pow(m.mu, 2 * k + 1);   // parent-edge scaling mu^(2k-1)
+        for (int64_t Jp = 0; Jp < nagg; ++Jp) {
+            const int32_t J = C.perm[Jp];
+            const int32_t a = F.pa[J], b = F.pb[J];
+            S.seg[Jp] = static_cast<int32_t>(F.perm.size());
+            F.perm.push_back(a);
+            F.perm.push_back(b);
+            // Elimination of T restricted to this aggregate (Section 3.3):
+            // M = s L_intra + pw diag(out).  Leftovers touch only a and b, so
+            // eliminating them leaves a 2x2 Schur complement
+            // [[alpha + cpl, -cpl], [-cpl, beta + cpl]] with nonnegative parts.
+            const double wab = edge_weight(F, a, b);
+            double alpha = pw * F.out[a], beta = pw * F.out[b], cpl = s * wab;
+            for (int64_t t = lstart[J]; t < lstart[J + 1]; ++t) {
+                const int32_t lu = left[t];
+                const double wla = edge_weight(F, lu, a), wlb = edge_weight(F, lu, b);
+                const double po = pw * F.out[lu];
+                const double d = s * (wla + wlb) + po;
+                const int64_t li = static_cast<int64_t>(F.perm.size()) - 2 * (Jp + 1);
+                S.lcf[3 * li + 0] = s * wla / d;
+                S.lcf[3 * li + 1] = s * wlb / d;
+                S.lcf[3 * li + 2] = 1.0 / d;
+                alpha += s * wla * po / d;
+                beta += s * wlb * po / d;
+                cpl += s * wla * s * wlb / d;
+                F.perm.push_back(lu);
+            }
+            const double det = alpha * beta + cpl * (alpha + beta);
+            S.inv[3 * Jp + 0] = (beta + cpl) / det;
+            S.inv[3 * Jp + 1] = cpl / det;
+            S.inv[3 * Jp + 2] = (alpha + cpl) / det;
+        }
+        S.seg[nagg] = static_cast<int32_t>(F.perm.size());
+        F.pos.assign(static_cast<size_t>(F.n), 0);
+        for (int64_t i = 0; i < F.n; ++i) F.pos[F.perm[i]] = static_cast<int32_t>(i);
+    }
+
+    // ---- level-1 Laplacian in tree order ---------------------------------
+    {
+        const HostLevel &F = m.lev[0];
+        HostCsr &A = m.L1;
+        A.n = F.n;
+        A.rp.assign(static_cast<size_t>(F.n) + 1, 0);
+        A.ci.resize(F.ci.size());
+        A.w.resize(F.w.size());
+        A.diag.resize(static_cast<size_t>(F.n));
+        std::vector<std::pair<int32_t, double>> row;
+        for (int64_t i = 0; i < F.n; ++i) {
+            const int32_t u = F.perm[i];
+            row.clear();
+            for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) row.push_back({F.pos[F.ci[p]], F.w[p]});
+            std::sort(row.begin(), row.end(),
+                      [](const auto &x, const auto &y) { return x.first < y.first; });
+            A.rp[i + 1] = A.rp[i] + static_cast<int64_t>(row.size());
+            for (size_t t = 0; t < row.size(); ++t) {
+                A.ci[A.rp[i] + t] = row[t].first;
+                A.w[A.rp[i] + t] = row[t].second;
+            }
+            A.diag[i] = F.deg[u];
+        }
+    }
+
+    // ---- top level: dense pseudo-inverse of mu^(2(l-1)) L_l ---------------
+    {
+        const HostLevel &T = m.lev[l - 1];
+        const int64_t nt = T.n;
+        if (nt > 4096) return LAP_ERR_UNSUPPORTED;
+        std::vector<double> A(static_cast<size_t>(nt * nt), 1.0 / static_cast<double>(nt));
+        for (int64_t u = 0; u < nt; ++u) {
+            A[u * nt + u] += T.deg[u];
+            for (int64_t p = T.rp[u]; p < T.rp[u + 1]; ++p) A[u * nt + T.ci[p]] -= T.w[p];
+        }
+        if (!spd_inverse(A, nt)) return LAP_ERR_BREAKDOWN;
+        const double inv_s = 1.0 / std::pow(m.mu, 2 * (l - 1));
+        for (auto &x : A) x = (x - 1.0 / static_cast<double>(nt)) * inv_s;
+        m.coarse_pinv = std::move(A);
+    }
+
+    // ---- number of edges of T --------------------------------------------
+    {
+        int64_t e = 0;
+        for (int k = 0; k + 1 < l; ++k) {
+            const HostLevel &F = m.lev[k];
+            for (int64_t u = 0; u < F.n; ++u) {
+                if (F.out[u] > 0.0) ++e;                           // parent edge
+                for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p)
+                    if (F.ci[p] > u && F.agg[F.ci[p]] == F.agg[u]) ++e;  // intra edge
+            }
+        }
+        e += m.lev[l - 1].rp[m.lev[l - 1].n] / 2;                  // top level
+        m.edges_T = e;
+    }
+
+    if (opt.prec == LAP_PREC_PEGP_INNER || opt.prec == LAP_PREC_PEGP_EXACT) build_pegp(m);
+    return LAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+void expanded_edges(const HostModel &m, int which, std::vector<int64_t> &I,
+                    std::vector<int64_t> &J, std::vector<double> &W)
+{
+    I.clear();
+    J.clear();
+    W.clear();
+    const int l = m.levels;
+    // tree-order expanded index -> hierarchy expanded index
+    std::vector<int64_t> back(static_cast<size_t>(m.offset[l]));
+    for (int k = 0; k < l; ++k)
+        for (int64_t i = 0; i < m.lev[k].n; ++i) back[m.offset[k] + i] = m.offset[k] + m.lev[k].perm[i];
+    std::vector<std::tuple<int64_t, int64_t, double>> e;
+    if (which == 0) {
+        const HostCsr &H = m.LH;
+        for (int64_t r = 0; r < H.n; ++r)
+            for (int64_t p = H.rp[r]; p < H.rp[r + 1]; ++p) {
+                int64_t a = back[r], b = back[H.ci[p]];
+                if (a < b) e.emplace_back(a, b, H.w[p]);
+            }
+    } else {
+        for (int k = 0; k < l; ++k) {
+            const HostLevel &F = m.lev[k];
+            const double s = std::pow(m.mu, 2 * k);
+            for (int64_t u = 0; u < F.n; ++u) {
+                for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) {
+                    const int32_t v = F.ci[p];
+                    if (v <= u) continue;
+                    if (k == l - 1 || F.agg[v] == F.agg[u])
+                        e.emplace_back(m.offset[k] + u, m.offset[k] + v, s * F.w[p]);
+                }
+                if (k + 1 < l && F.out[u] > 0.0)
+                    e.emplace_back(m.offset[k] + u, m.offset[k + 1] + F.agg[u],
+                                   std::pow(m.mu, 2 * k + 1) * F.out[u]);
+            }
+        }
+    }
+    std::sort(e.begin(), e.end());
+    for (auto &t : e) {
+        I.push_back(std::get<0>(t));
+        J.push_back(std::get<1>(t));
+        W.push_back(std::get<2>(t));
+    }
+}
+
+}  // namespace lap

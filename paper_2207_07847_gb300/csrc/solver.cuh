@@ -1,0 +1,65 @@
+// Solver handle and the host-side entry points shared by the C ABI files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <vector>
+
+#include "device_model.cuh"
+#include "lap_internal.h"
+
+struct lap_handle_s {
+    lap::HostModel m;
+    bool host_only = false;
+    int device = 0;
+    int sms = 0;
+    int grid_cap = 0;                 // resident 256-thread blocks on the device
+    cudaStream_t s = nullptr;         // private stream (graphs are captured on it)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<std::unique_ptr<lap::DevBuf>> bufs;
+    int64_t device_bytes = 0;
+
+    lap::DevCsr<double> L64;
+    lap::DevCsr<float> L32;
+    lap::DevMsp<double> M64;
+    lap::DevMsp<float> M32;
+    lap::DevCsr<double> H64;          // L_H (PEGP), expanded tree order
+    lap::DevCsr<float> H32;
+    int tpr = 8, tprH = 8;            // threads per CSR row
+
+    int *perm1 = nullptr;             // tree position -> input vertex id
+    int64_t *xmap = nullptr;          // tree expanded index -> hierarchy expanded index
+    double *bs = nullptr;             // centred right-hand side (tree order)
+    double *bin = nullptr, *xout = nullptr;   // staging for host-vector solves
+
+    lap::CgVectors<double> w64;       // FP64 CG on L
+    lap::CgVectors<float> w32;        // FP32 inner CG of mixed precision
+    lap::CgVectors<double> e64;       // expanded-space CG (PEGP inner solve)
+    lap::CgVectors<float> e32;
+    lap::CgState st64, st32, ste64, ste32, stb;   // scalars + reduction scratch
+    lap::CgScalars *hsc = nullptr;    // pinned host mirror of one CgScalars
+
+    cudaGraphExec_t g_iter64 = nullptr, g_iter32 = nullptr;
+    cudaGraphExec_t g_in64 = nullptr, g_in32 = nullptr;   // PEGP inner-iteration chunks
+    int g_iter_k = 0, g_in_k = 0;
+};
+
+namespace lap {
+
+lap_status upload_model(lap_handle_s &h, cudaStream_t user);
+void destroy_handle(lap_handle_s &h);
+
+lap_status block_laplacian(lap_handle_s &h, const double *x, double *y, cudaStream_t user);
+lap_status block_precond(lap_handle_s &h, const double *r, double *z, cudaStream_t user);
+lap_status block_restrict(lap_handle_s &h, const double *r, double *rt, cudaStream_t user);
+lap_status block_prolong(lap_handle_s &h, const double *yt, double *z, cudaStream_t user);
+lap_status block_msp_solve(lap_handle_s &h, const double *rt, double *yt, cudaStream_t user);
+lap_status block_pegp(lap_handle_s &h, const double *xt, double *yt, cudaStream_t user);
+
+lap_status solve_device(lap_handle_s &h, const double *b, double *x, cudaStream_t user,
+                        lap_solve_info &info);
+lap_status solve_host(lap_handle_s &h, const double *b, double *x, cudaStream_t user,
+                      lap_solve_info &info);
+
+}  // namespace lap

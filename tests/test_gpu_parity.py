@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path against the oracle, element by element.
+
+Every test calls the library through its C ABI (ctypes binding) on device
+tensors and compares with the oracle on the same seeded inputs.  Tolerances:
+
+* single operator applications in FP64 (L x, P(mu)^T r, P(mu) y, L_H x, the MSP
+  and PEGP preconditioners): the difference is rounding of sums taken in
+  another order, bounded by a few ulps of the magnitudes summed;
+* FP64 solves: iteration counts within +-1 of the oracle's and the two
+  solutions agree in the residual norm, ||L (x_gpu - x_oracle)|| <= 1e-9 ||Pi b||,
+  with both true relative residuals <= 1e-8;
+* mixed precision: true relative residual <= 1e-8 and the solution within the
+  error that residual allows of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle.expanded import laplacian
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2207_07847_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build_library()
+    P.lib()
+    P.set_torch_allocator()
+    yield
+    torch.cuda.synchronize()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def solve_gpu(h, b):
+    x = torch.empty_like(b)
+    info = P.lap_pcg_solve(h, b, x)
+    return x, info
+
+
+SMALL = {
+    "grid2d_64": lambda: gg.grid2d(64, weights="uniform", lo=1.0, hi=2.0, seed=1),
+    "grid3d_20": lambda: gg.grid3d(20, 19, 18, weights="loguniform", lo=1e-3, hi=1e3, seed=3),
+    "chunglu_4k": lambda: gg.chung_lu(4096, avg_deg=16, seed=4),
+    "rmat_11": lambda: gg.rmat(11, 16, seed=5),
+    "rgg_3k": lambda: gg.rgg(3000, seed=6),
+}
+
+
+@pytest.fixture(scope="module", params=list(SMALL))
+def case(request):
+    g = SMALL[request.param]()
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=17)
+    ops = oracle.expanded_operators(ho, 0.8, with_LG=False)
+    return request.param, g, ho, ops
+
+
+# --- single operators ---------------------------------------------------------------------
+
+def test_laplacian_apply(case):
+    name, g, ho, ops = case
+    h = P.lap_setup(g, seed=17)
+    x = gg.rhs(g.n, seed=1)
+    y = dev(np.zeros(g.n))
+    P.lap_laplacian_apply(h, dev(x), y)
+    want = ops.L @ x
+    scale = abs(ops.L) @ np.abs(x)
+    assert np.all(np.abs(host(y) - want) <= 1e-14 * scale + 1e-300)
+
+
+def test_restrict_and_prolong(case):
+    name, g, ho, ops = case
+    h = P.lap_setup(g, seed=17, mu=0.8)
+    r = gg.rhs(g.n, seed=2)
+    rt = dev(np.zeros(ops.ntilde))
+    P.lap_restrict_apply(h, dev(r), rt)
+    want = ops.Pmu.T @ r
+    scale = abs(ops.Pmu).T @ np.abs(r)
+    assert np.all(np.abs(host(rt) - want) <= 1e-13 * scale)
+    yt = gg.rhs(ops.ntilde, seed=3)
+    z = dev(np.zeros(g.n))
+    P.lap_prolong_apply(h, dev(yt), z)
+    want = ops.Pmu @ yt
+    scale = abs(ops.Pmu) @ np.abs(yt)
+    assert np.all(np.abs(host(z) - want) <= 1e-13 * scale)
+
+
+def test_msp_solve_solves_the_sparsifier(case):
+    """y~ with L_T y~ = r~ (Section 3.3), r~ = P(mu)^T Pi r."""
+    name, g, ho, ops = case
+    h = P.lap_setup(g, seed=17, mu=0.8)
+    r = gg.rhs(g.n, seed=4)
+    rt = ops.Pmu.T @ (r - r.mean())
+    yt = dev(np.zeros(ops.ntilde))
+    P.lap_msp_solve(h, dev(rt), yt)
+    y = host(yt)
+    res = ops.LT @ y - rt
+    assert np.linalg.norm(res) <= 1e-11 * (abs(ops.LT) @ np.abs(y)).max() * np.sqrt(ops.ntilde)
+    # equal to the oracle's sparse solve up to a constant vector
+    from oracle.solve import _GroundedSolver
+    want = _GroundedSolver(ops.LT)(rt)
+    d = (y - y.mean()) - want
+    assert np.linalg.norm(d) <= 1e-9 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("kind", ["msp", "none", "pegp_inner"])
+def test_preconditioner_apply(case, kind):
+    name, g, ho, ops = case
+    if kind == "pegp_inner" and name not in ("grid2d_64", "grid3d_20"):
+        pytest.skip("PEGP inner solve checked on the grid cases")
+    h = P.lap_setup(g, seed=17, mu=0.8, prec=kind, inner_tol=1e-10, inner_maxit=2000)
+    r = gg.rhs(g.n, seed=5)
+    z = dev(np.zeros(g.n))
+    P.lap_precond_apply(h, dev(r), z)
+    M = oracle.OraclePreconditioner(kind if kind != "none" else "none",
+                                    ops if kind != "none" else None, inner_tol=1e-10,
+                                    inner_maxit=2000)
+    want = M(r)
+    got = host(z)
+    tol = 1e-10 if kind != "pegp_inner" else 1e-8
+    assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
+    assert abs(got.mean()) <= 1e-12 * np.abs(got).max()
+
+
+def test_pegp_apply(case):
+    name, g, ho, ops = case
+    if name not in ("grid2d_64", "grid3d_20", "rgg_3k"):
+        pytest.skip("L_H matvec checked on three families")
+    h = P.lap_setup(g, seed=17, mu=0.8, prec="pegp_inner")
+    xt = gg.rhs(ops.ntilde, seed=6)
+    yt = dev(np.zeros(ops.ntilde))
+    P.lap_pegp_apply(h, dev(xt), yt)
+    want = ops.LH @ xt
+    scale = abs(ops.LH) @ np.abs(xt)
+    assert np.all(np.abs(host(yt) - want) <= 1e-12 * scale)
+
+
+# --- solves ----------------------------------------------------------------------------------
+
+def _oracle_solve(g, b, kind, mu, **kw):
+    return oracle.solve(g, b, kind, mu=mu, seed=17, **kw)
+
+
+@pytest.mark.parametrize("kind", ["msp", "none"])
+def test_fp64_solve_parity(case, kind):
+    name, g, ho, ops = case
+    b = gg.rhs(g.n, seed=7)
+    h = P.lap_setup(g, seed=17, mu=0.8, prec=kind, maxit=3000)
+    x, info = solve_gpu(h, dev(b))
+    ref = _oracle_solve(g, b, kind, 0.8, maxit=3000)
+    assert info.status == 0 and ref.converged
+    assert abs(info.iterations - ref.iters) <= 1, (info.iterations, ref.iters)
+    xg = host(x)
+    bp = b - b.mean()
+    assert np.linalg.norm(bp - ops.L @ xg) <= 1e-8 * np.linalg.norm(bp)
+    assert np.linalg.norm(ops.L @ (xg - ref.x)) <= 1e-9 * np.linalg.norm(bp)
+    assert abs(xg.mean()) <= 1e-12 * np.abs(xg).max()
+    assert info.relres <= 1e-8
+
+
+def test_fp64_pegp_inner_parity():
+    g = SMALL["grid2d_64"]()
+    b = gg.rhs(g.n, seed=8)
+    h = P.lap_setup(g, seed=17, mu=0.8, prec="pegp_inner", inner_tol=1e-6, inner_maxit=500)
+    x, info = solve_gpu(h, dev(b))
+    ref = _oracle_solve(g, b, "pegp_inner", 0.8, inner_tol=1e-6, inner_maxit=500)
+    assert info.status == 0 and ref.converged
+    assert abs(info.iterations - ref.iters) <= 1
+    L = laplacian(g.adjacency())
+    bp = b - b.mean()
+    xg = host(x)
+    assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
+    assert np.linalg.norm(L @ (xg - ref.x)) <= 1e-9 * np.linalg.norm(bp)
+
+
+@pytest.mark.parametrize("kind", ["msp", "pegp_inner"])
+def test_mixed_precision_solve(kind):
+    g = SMALL["grid3d_20"]()
+    b = gg.rhs(g.n, seed=9)
+    h = P.lap_setup(g, seed=17, mu=0.8, prec=kind, precision="mixed", maxit=5000)
+    x, info = solve_gpu(h, dev(b))
+    assert info.status == 0, info.as_dict()
+    assert info.relres <= 1e-8 and info.refinements >= 1
+    ref = _oracle_solve(g, b, kind if kind == "msp" else "msp", 0.8, maxit=5000)
+    L = laplacian(g.adjacency())
+    bp = b - b.mean()
+    xg = host(x)
+    assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
+    assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+
+
+# --- edge cases --------------------------------------------------------------------------------
+
+def test_zero_and_constant_rhs_give_zero():
+    g = gg.grid2d(9, 7, weights="uniform", seed=2)
+    h = P.lap_setup(g, seed=1)
+    for b in (np.zeros(g.n), np.full(g.n, 3.5)):
+        x, info = solve_gpu(h, dev(b))
+        assert info.status == 0
+        assert np.all(host(x) == 0.0)
+
+
+def test_single_level_graph_is_solved_directly():
+    g = gg.path(20, w=np.linspace(1, 3, 19))
+    h = P.lap_setup(g, seed=1)
+    assert P.lap_get_hierarchy_info(h)["levels"] == 1
+    b = gg.rhs(g.n, seed=3)
+    x, info = solve_gpu(h, dev(b))
+    assert info.status == 0 and info.iterations <= 2
+    L = laplacian(g.adjacency()).toarray()
+    xs = np.linalg.lstsq(L, b - b.mean(), rcond=None)[0]
+    xs -= xs.mean()
+    np.testing.assert_allclose(host(x), xs, atol=1e-10 * np.abs(xs).max())
+
+
+@pytest.mark.parametrize("n", [2, 3, 33, 65, 1000, 4097])
+def test_ragged_path_and_ring_sizes(n):
+    for g in (gg.path(n, w=np.linspace(1, 2, n - 1)), gg.ring(max(n, 5), 2, weights="uniform", seed=n)):
+        b = gg.rhs(g.n, seed=n)
+        h = P.lap_setup(g, seed=3, coarse_max=2, maxit=5000)
+        x, info = solve_gpu(h, dev(b))
+        ref = _oracle_solve(g, b, "msp", 0.8, coarse_max=2, maxit=5000)
+        assert info.status == 0 and ref.converged
+        assert abs(info.iterations - ref.iters) <= 1
+        L = laplacian(g.adjacency())
+        bp = b - b.mean()
+        assert np.linalg.norm(L @ (host(x) - ref.x)) <= 1e-9 * np.linalg.norm(bp)
+
+
+def test_solves_are_deterministic_and_stream_safe():
+    g = SMALL["grid3d_20"]()
+    b = dev(gg.rhs(g.n, seed=11))
+    h = P.lap_setup(g, seed=17)
+    x1, i1 = solve_gpu(h, b)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        x2 = torch.empty_like(b)
+        i2 = P.lap_pcg_solve(h, b, x2, stream=s)
+    s.synchronize()
+    assert i1.iterations == i2.iterations
+    assert torch.equal(x1, x2)
+    xh = np.empty(g.n)
+    i3 = P.lap_pcg_solve_host(h, host(b), xh)
+    assert i3.status == 0 and np.array_equal(xh, host(x1))
+
+
+def test_maxit_reports_no_convergence():
+    g = SMALL["grid2d_64"]()
+    h = P.lap_setup(g, seed=17, prec="none", maxit=5)
+    x, info = solve_gpu(h, dev(gg.rhs(g.n, seed=1)))
+    assert info.status == 7 and info.iterations == 5 and info.relres > 1e-8
+
+
+# --- full-size workload: properties that hold at any size -----------------------------------
+
+@pytest.mark.slow
+def test_full_size_grid3d_solve_properties():
+    """The 128^3 log-uniform grid of the benchmark: Laplacian rows sampled
+    against the oracle's definition, P(mu) adjointness, and the true residual of
+    the FP64 and mixed solves recomputed independently with torch sparse ops."""
+    g = gg.grid3d(128, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    h = P.lap_setup(g, seed=1, mu=0.8)
+    rng = np.random.default_rng(0)
+    x = gg.rhs(g.n, seed=12)
+    y = dev(np.zeros(g.n))
+    P.lap_laplacian_apply(h, dev(x), y)
+    yh = host(y)
+    for i in rng.integers(0, g.n, 2000):
+        cols = g.col_idx[g.row_ptr[i]:g.row_ptr[i + 1]]
+        ws = g.w[g.row_ptr[i]:g.row_ptr[i + 1]]
+        want = ws.sum() * x[i] - ws @ x[cols]
+        assert abs(yh[i] - want) <= 1e-14 * (2 * ws.sum() * np.abs(x).max())
+    info = P.lap_get_hierarchy_info(h)
+    r = gg.rhs(g.n, seed=13)
+    yt = gg.rhs(info["ntilde"], seed=14)
+    rt = dev(np.zeros(info["ntilde"]))
+    z = dev(np.zeros(g.n))
+    P.lap_restrict_apply(h, dev(r), rt)
+    P.lap_prolong_apply(h, dev(yt), z)
+    lhs, rhs = float(host(rt) @ yt), float(r @ host(z))
+    assert abs(lhs - rhs) <= 1e-10 * (np.abs(host(rt)) @ np.abs(yt))
+    A = torch.sparse_csr_tensor(torch.as_tensor(g.row_ptr), torch.as_tensor(g.col_idx.astype(np.int64)),
+                                torch.as_tensor(g.w), size=(g.n, g.n)).to("cuda")
+    deg = dev(np.asarray(g.adjacency().sum(axis=1)).ravel())
+    b = dev(gg.rhs(g.n, seed=15))
+    bp = b - b.mean()
+    for precision in ("fp64", "mixed"):
+        hh = P.lap_setup(g, seed=1, mu=0.8, precision=precision)
+        xg, inf = solve_gpu(hh, b)
+        assert inf.status == 0
+        res = bp - (deg * xg - (A @ xg.unsqueeze(1)).squeeze(1))
+        assert float(torch.linalg.norm(res) / torch.linalg.norm(bp)) <= 1e-8
+        hh.close()

@@ -1,0 +1,147 @@
+"""Host-side logic of the solver library, checked without a GPU.
+
+The library's setup stage (validation, matching hierarchy, sparsifier T and
+PEGP H construction) runs on the host; with ``host_only=1`` it touches no GPU,
+so its integer outputs can be compared bit-for-bit with the oracle here.
+"""
+import re
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+P = pytest.importorskip("paper_2207_07847_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2207_07847_gb300 import build
+    build.build()
+    P.lib()
+
+
+def _declared_functions():
+    with open(P.os.path.join(P.os.path.dirname(P._HERE), "include", "lap.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lap_[a-z_]+)\s*\(", src)) - {"lap_alloc_fn", "lap_free_fn",
+                                                                   "lap_done_cb"})
+
+
+def test_library_exports_every_declared_function():
+    names = _declared_functions()
+    assert len(names) >= 20
+    lib = P.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert {s[0] for s in P.SIGNATURES} == set(names)
+
+
+def test_options_defaults_and_status_strings():
+    o = P.make_options()
+    assert o.prec == 1 and o.precision == 0 and o.mu == 0.8 and o.coarse_max == 32
+    assert o.tol == 1e-8 and o.maxit == 1000
+    for s in range(13):
+        assert P.lib().lap_status_string(s)
+
+
+GRAPHS = [
+    ("grid2d", lambda: gg.grid2d(64, weights="uniform", lo=1, hi=2, seed=1)),
+    ("grid3d", lambda: gg.grid3d(14, 13, 12, weights="loguniform", lo=1e-3, hi=1e3, seed=3)),
+    ("chunglu", lambda: gg.chung_lu(3000, avg_deg=16, seed=4)),
+    ("rmat", lambda: gg.rmat(11, 16, seed=5)),
+    ("rgg", lambda: gg.rgg(2500, seed=6)),
+    ("ws", lambda: gg.watts_strogatz(1024, seed=2)),
+]
+
+
+@pytest.mark.parametrize("name,make", GRAPHS, ids=[g[0] for g in GRAPHS])
+@pytest.mark.parametrize("seed,order_random,coarse_max", [(7, 1, 32), (0, 0, 2), (123, 1, 5)])
+def test_hierarchy_bit_exact_with_oracle(name, make, seed, order_random, coarse_max):
+    g = make()
+    h = P.lap_setup(g, host_only=1, seed=seed, order_random=order_random, coarse_max=coarse_max)
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, coarse_max=coarse_max, seed=seed,
+                                order_random=bool(order_random))
+    info = P.lap_get_hierarchy_info(h)
+    assert info["level_size"] == ho.sizes
+    assert info["ntilde"] == ho.ntilde
+    for k in range(ho.levels - 1):
+        agg, pa, pb = P.lap_get_aggregates(h, k + 1)
+        np.testing.assert_array_equal(agg, ho.agg[k])
+        np.testing.assert_array_equal(pa, ho.pair_a[k])
+        np.testing.assert_array_equal(pb, ho.pair_b[k])
+
+
+@pytest.mark.parametrize("name,make", GRAPHS[:4], ids=[g[0] for g in GRAPHS[:4]])
+@pytest.mark.parametrize("mu", [0.8, 0.3])
+def test_sparsifier_and_pegp_edges_bit_exact(name, make, mu):
+    g = make()
+    h = P.lap_setup(g, host_only=1, seed=11, mu=mu, prec="pegp_inner")
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=11)
+    ops = oracle.expanded_operators(ho, mu, with_LG=False)
+    # The oracle forms each weight as a sum of signed terms (P^T L P); its rounding
+    # error is bounded by a few ulps of |P|^T |L| |P| at that entry (H_scale).
+    Hscale = dict(zip(zip(ops.H_edges[0].tolist(), ops.H_edges[1].tolist()), ops.H_scale))
+    for which, ref in ((1, ops.T_edges), (0, ops.H_edges)):
+        i, j, w = P.lap_get_expanded_edges(h, which)
+        np.testing.assert_array_equal(i, ref[0])
+        np.testing.assert_array_equal(j, ref[1])
+        scale = np.array([Hscale[(a, b)] for a, b in zip(i.tolist(), j.tolist())])
+        assert np.all(np.abs(w - ref[2]) <= 1e-13 * np.abs(ref[2]) + 1e-12 * scale)
+    assert P.lap_get_hierarchy_info(h)["edges_T"] == len(ops.T_edges[0])
+
+
+def test_library_reproduces_table_level_sizes():
+    for n in (16, 64, 256, 1024):
+        s = int(round(n ** 0.5))
+        for g in (gg.grid2d(s), gg.ring(n, 2)):
+            h = P.lap_setup(g, host_only=1, order_random=0, coarse_max=2)
+            info = P.lap_get_hierarchy_info(h)
+            assert info["level_size"] == [n >> k for k in range(info["levels"])]
+
+
+def _status(rp, ci, w, **kw):
+    return P.lap_setup_status(rp, ci, w, host_only=1, **kw)
+
+
+def test_validation_rejects_bad_input():
+    g = gg.grid2d(4)
+    rp, ci, w = g.row_ptr.copy(), g.col_idx.copy(), g.w.copy()
+    assert _status(rp, ci, w) == 0
+    w2 = w.copy()
+    w2[0] = 2.0
+    assert _status(rp, ci, w2) == 2                   # weight asymmetry
+    w3 = w.copy()
+    w3[3] = -1.0
+    assert _status(rp, ci, w3) == 4                   # bad weight
+    w4 = w.copy()
+    w4[5] = np.nan
+    assert _status(rp, ci, w4) == 4
+    ci2 = ci.copy()
+    ci2[0] = 0                                        # self-loop at vertex 0
+    assert _status(rp, ci2, w) == 1
+    ci3 = ci.copy()
+    ci3[1] = ci3[0]                                   # duplicate entry
+    assert _status(rp, ci3, w) == 1
+    ci4 = ci.copy()
+    ci4[0] = 99                                       # out of range
+    assert _status(rp, ci4, w) == 1
+    two = gg.from_edges(4, [0, 2], [1, 3])            # two components
+    assert _status(two.row_ptr, two.col_idx, two.w) == 3
+    assert _status(np.array([0]), np.array([], np.int32), np.array([])) == 1   # n = 0
+    assert _status(rp, ci, w, mu=1.5) == 1
+    assert _status(rp, ci, w, tol=0.0) == 1
+
+
+def test_single_level_when_graph_is_small():
+    g = gg.path(5, w=[1.0, 2.0, 3.0, 4.0])
+    h = P.lap_setup(g, host_only=1)
+    assert P.lap_get_hierarchy_info(h)["levels"] == 1
+
+
+def test_host_only_handle_refuses_device_work():
+    g = gg.grid2d(8)
+    h = P.lap_setup(g, host_only=1)
+    assert P.lib().lap_pcg_solve(h, 8, 16, None, None) == 1

@@ -424,7 +424,8 @@ lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int
     const auto &st = Sel<V>::st(h);
     const auto &M = Sel<V>::M(h);
     const int64_t n = M.off[1];
-    if (!is_pegp(h)) {
+    if (!is_pegp(h) || M.levels == 1) {
+        // one level: H = T = G, so the dense top-level solve is PEGP exactly
         precond_msp<V>(h, M, w, st, update, is_plain(h), s);
         return LAP_OK;
     }

@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: preconditioned CG solves per second at relative residual 1e-8.
+
+Workload (one "step" = one full solve of L x = b, setup excluded): the 3D
+128^3 7-point grid graph (2,097,152 vertices, 6,242,304 edges) with edge
+weights log-uniform in [1e-3, 1e3], one N(0,1) right-hand side per step
+(projected to mean zero by the solver), PCG preconditioned by the paper's
+PEGP (inner CG on L_H with the MSP sparsifier, mu = 0.8), mixed precision:
+FP32 matvecs/sweeps with FP32 accumulation, FP64 dots, scalars, projection,
+coarsest solve and iterative-refinement residuals.  The plain FP64 solve of
+the same system is measured beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own copy ("replicas only"; no
+collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCG solves/s at relres 1e-8 and HBM GB/s vs peak; p50/p99 latency vs plain FP64"
+WORKLOAD = {
+    "name": "grid3d_128^3_loguniform[1e-3,1e3]_PEGP_mu0.8",
+    "nx": 128, "wlo": 1e-3, "whi": 1e3, "wseed": 3, "prec": "pegp_inner", "mu": 0.8,
+    "tol": 1e-8, "inner_tol": 1e-1, "setup_seed": 1,
+}
+CPU_SAMPLE_NX = 24        # oracle sample: the same generator at 24^3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=WORKLOAD["nx"], help="grid side (128 = the workload)")
+    ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["pegp_inner", "msp", "none"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.file.read().splitlines() if ln.strip()]
+        os.unlink(self.file.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_worker(spec_json):
+    """Runs in a single-threaded subprocess: the oracle solve on the sample."""
+    spec = json.loads(spec_json)
+    import numpy as np
+
+    import graphgen as gg
+    import oracle
+    g = gg.grid3d(spec["nx"], weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
+                  seed=WORKLOAD["wseed"])
+    M = oracle.make_preconditioner(spec["prec"], g, mu=WORKLOAD["mu"], seed=WORKLOAD["setup_seed"],
+                                   inner_tol=WORKLOAD["inner_tol"], inner_maxit=200)
+    from oracle.solve import _laplacian_of
+    L = M.ops.L if M.ops is not None else _laplacian_of(g)
+    times, work = [], []
+    for i in range(spec["reps"]):
+        b = gg.rhs(g.n, seed=100 + i)
+        M.inner_iters.clear()
+        t0 = time.perf_counter()
+        res = oracle.pcg(L, b, M, tol=WORKLOAD["tol"], maxit=5000, flexible=M.flexible)
+        times.append(time.perf_counter() - t0)
+        work.append(res.iters + sum(M.inner_iters))
+        assert res.converged
+    print(json.dumps({"n": g.n, "times": times, "work": work}))
+
+
+def run_oracle(nx, prec, reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    spec = json.dumps({"nx": nx, "prec": prec, "reps": reps})
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
+                         capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(prec, n_full, work_full, reps=1):
+    """Oracle solves/s on the 24^3 sample, scaled to the full workload by vertex
+    count and by (outer + inner) iterations per solve."""
+    r = run_oracle(CPU_SAMPLE_NX, prec, reps)
+    t = statistics.median(r["times"])
+    w = statistics.median(r["work"])
+    scaled = (1.0 / t) * (r["n"] * w) / (n_full * work_full)
+    return {"value": scaled, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy, 1 thread) full solve of the same generator at "
+                       f"{CPU_SAMPLE_NX}^3 = {r['n']} vertices: {t:.2f} s for {w} outer+inner "
+                       f"iterations; scaled by vertices and iterations to the {n_full}-vertex "
+                       f"workload at {work_full} iterations"),
+            "sample_solves_per_s": 1.0 / t}
+
+
+# ---------------------------------------------------------------------------
+def bench_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        P.build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    P.lib()
+    P.set_torch_allocator()
+
+    g = gg.grid3d(args.nx, weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
+                  seed=WORKLOAD["wseed"])
+    t0 = time.perf_counter()
+    h = P.lap_setup(g, prec=args.prec, mu=WORKLOAD["mu"], precision="mixed",
+                    seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"],
+                    inner_tol=WORKLOAD["inner_tol"], maxit=5000)
+    setup_s = time.perf_counter() - t0
+    info_h = P.lap_get_hierarchy_info(h)
+    K, W = args.steps, args.warmup
+    rhs = [gg.rhs(g.n, seed=100 + i + 1000 * rank) for i in range(K + W)]
+    dB = [torch.as_tensor(b, device=dev) for b in rhs]
+    hB = [torch.as_tensor(b).pin_memory() for b in rhs]
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    xh = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def timed(precision, host=False):
+        P.lap_update_options(h, precision=precision)
+        for i in range(W):
+            inf = (P.lap_pcg_solve_host(h, hB[i], xh) if host else P.lap_pcg_solve(h, dB[i], x))
+            assert inf.status == 0, inf.as_dict()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos, lat = [], []
+        ev0.record(stream)
+        for i in range(W, W + K):
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            inf = (P.lap_pcg_solve_host(h, hB[i], xh) if host else P.lap_pcg_solve(h, dB[i], x))
+            e_b.record(stream)
+            assert inf.status == 0, inf.as_dict()
+            infos.append(inf)
+            lat.append((e_a, e_b))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        lats = sorted(a.elapsed_time(b) for a, b in lat)
+        return ms, infos, lats
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ms_mixed, inf_mixed, lat_mixed = timed("mixed")
+    clk = clocks.stop()
+    ms_fp64, inf_fp64, lat_fp64 = timed("fp64")
+    ms_e2e, inf_e2e, _ = timed("mixed", host=True)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+
+    # dominant kernel: the FP32 L_H matvec of the inner solves (PEGP) or the FP32
+    # L matvec (MSP / none); timed back to back on the solve's data with CUDA
+    # events on the library's stream
+    P.lap_update_options(h, precision="mixed")
+    kern = "spmv_LH" if args.prec == "pegp_inner" else "spmv_L"
+    kms, kbytes = P.lap_kernel_bench(h, kern, 1, 20)
+    peak, peak_kind = measured_peaks()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    other = {}
+    for name, prec in (("spmv_L_f32", ("spmv_L", 1)), ("spmv_L_f64", ("spmv_L", 0)),
+                       ("msp_sweep_f32", ("msp_sweep", 1)), ("update_up1_f32", ("update_up1", 1))):
+        m_, b_ = P.lap_kernel_bench(h, prec[0], prec[1], 20)
+        other[name] = {"us": round(m_ * 1e3, 2), "GB/s": round(b_ / (m_ * 1e-3) / 1e9, 1)}
+    if args.prec == "pegp_inner":
+        m_, b_ = P.lap_kernel_bench(h, "spmv_LH", 0, 10)
+        other["spmv_LH_f64"] = {"us": round(m_ * 1e3, 2), "GB/s": round(b_ / (m_ * 1e-3) / 1e9, 1)}
+
+    value = K * world / (ms_mixed * 1e-3)
+    fp64_value = K * world / (ms_fp64 * 1e-3)
+    e2e_value = K * world / (ms_e2e * 1e-3)
+    it_mixed = statistics.median(i.iterations for i in inf_mixed)
+    it_fp64 = statistics.median(i.iterations for i in inf_fp64)
+    inner_fp64 = statistics.median(i.inner_iterations for i in inf_fp64)
+    result = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_mixed / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"] if args.nx == 128 else f"grid3d_{args.nx}^3",
+                   "n": g.n, "nnz": info_h["nnz"], "levels": info_h["levels"],
+                   "ntilde": info_h["ntilde"], "nnz_H": info_h["nnz_H"],
+                   "preconditioner": args.prec, "mu": WORKLOAD["mu"], "tol": WORKLOAD["tol"],
+                   "inner_tol": WORKLOAD["inner_tol"], "precision": "mixed (FP32 matvec/sweeps, "
+                   "FP64 dots/scalars/refinement residuals)", "rhs": "N(0,1), one per step",
+                   "l2": "inputs larger than L2 (L_H alone is "
+                   f"{info_h['nnz_H'] * 8 / 1e9:.1f} GB in FP32)", "parallelism": f"replicas x{world}",
+                   "setup_s": round(setup_s, 2)},
+        "latency_ms": {"p50": pct(lat_mixed, 0.5), "p99": pct(lat_mixed, 0.99)},
+        "iterations": {"outer": it_mixed, "refinements": statistics.median(i.refinements for i in inf_mixed),
+                       "inner": statistics.median(i.inner_iterations for i in inf_mixed),
+                       "relres_max": max(i.relres for i in inf_mixed)},
+        "fp64": {"value": fp64_value, "unit": "solves/s", "latency_ms": {
+            "p50": pct(lat_fp64, 0.5), "p99": pct(lat_fp64, 0.99)}, "iterations": it_fp64,
+            "inner_iterations": inner_fp64, "relres_max": max(i.relres for i in inf_fp64)},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": g.n * 8,
+                "d2h_bytes_per_step": g.n * 8},
+        "gpu_launches": int(sum(i.kernel_launches for i in inf_mixed)),
+        "roofline": {"bound": "hbm", "kernel": f"{kern} (FP32)", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_kind": peak_kind, "bytes_per_launch": kbytes,
+                     "us_per_launch": round(kms * 1e3, 2), "traffic": None},
+        "kernels": other,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            result["cpu_baseline"] = cpu_baseline(args.prec, g.n, it_fp64 + inner_fp64)
+        except Exception as e:          # the baseline is reported, never fatal
+            result["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    h.close()
+    return result
+
+
+def bench_reference(args):
+    """The oracle as the reference arm: each step one full oracle solve of the
+    24^3 sample, reported in solves/s scaled to the 128^3 workload."""
+    import graphgen as gg
+    n_full = args.nx ** 3
+    reps = args.steps + args.warmup
+    small = run_oracle(CPU_SAMPLE_NX * 2 // 3, args.prec, 1)
+    r = run_oracle(CPU_SAMPLE_NX, args.prec, reps)
+    times = r["times"][args.warmup:]
+    work = statistics.median(r["work"])
+    # iterations per solve at full size: power law in the grid side fitted to
+    # the two sample sizes (16^3 and 24^3)
+    expo = math.log(work / statistics.median(small["work"])) / math.log(1.5)
+    work_full = work * (args.nx / CPU_SAMPLE_NX) ** expo
+    t = sum(times)
+    value = len(times) / t * (r["n"] * work) / (n_full * work_full)
+    return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD["name"], "sample": f"{CPU_SAMPLE_NX}^3"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle full solves at {CPU_SAMPLE_NX}^3 ({r['n']} vertices, "
+                                       f"{work} outer+inner iterations), scaled by vertices and by "
+                                       f"iterations extrapolated as (side)^{expo:.2f} from 16^3 and "
+                                       f"24^3 to {work_full:.0f}"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(bench_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    res = bench_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -106,7 +106,8 @@ typedef struct lap_solve_info {
     int32_t refinements;       /* LAP_MIXED: FP64 residual refreshes              */
     int32_t inner_iterations;  /* PEGP_INNER: total inner CG iterations           */
     int32_t restarts;          /* restarts from a recomputed true residual        */
-    int32_t reserved0;
+    int32_t kernel_launches;   /* CUDA kernels launched by the call (graph nodes
+                                  counted one by one)                              */
     double relres;             /* true relative residual of the returned x        */
     double relres_recurrence;  /* recurrence estimate at exit                     */
     double seconds;            /* host wall time of the call                      */
@@ -161,6 +162,30 @@ lap_status lap_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
 
 /* Release a handle and its device memory (synchronises its streams). NULL is ok. */
 void lap_destroy(lap_handle h);
+
+/*
+ * Change the solve-time options of a handle: tol, maxit, inner_tol,
+ * inner_maxit, refine_tol, max_refine, check_every, timeout_s and precision.
+ * precision may switch to LAP_MIXED only if the handle was set up with
+ * LAP_MIXED (FP32 copies exist); switching to LAP_FP64 is always allowed.
+ * Setup-time fields (prec, mu, coarse_max, max_levels, seed, order_random,
+ * spmv_tpr, host_only) are ignored.
+ */
+lap_status lap_update_options(lap_handle h, const lap_options *opts);
+
+/*
+ * Time one kernel of the solve on the handle's data, for roofline reports:
+ *   kernel 0: CSR matvec with L          kernel 1: CSR matvec with L_H (PEGP)
+ *   kernel 2: the whole MSP sweep B r    kernel 3: fused CG update + level-1
+ *                                                  restriction/elimination
+ * in FP64 (precision 0) or FP32 (precision 1, LAP_MIXED handles).  Runs `reps`
+ * back-to-back launches (sequences for kernel 2) on the handle's stream
+ * timed by CUDA events and writes the mean milliseconds per launch and the
+ * algorithmic bytes of one launch (every array the kernel must touch, read
+ * or written once).  Overwrites the handle's solve workspace.
+ */
+lap_status lap_kernel_bench(lap_handle h, int32_t kernel, int32_t precision, int32_t reps,
+                            double *ms_per_launch, double *bytes_per_launch);
 
 /* Sizes of the hierarchy built by lap_setup. */
 lap_status lap_get_hierarchy_info(lap_handle h, lap_hierarchy_info *info);
@@ -221,6 +246,15 @@ lap_status lap_pegp_apply(lap_handle h, const double *d_xt, double *d_yt, void *
  */
 lap_status lap_pcg_solve(lap_handle h, const double *d_b, double *d_x, void *stream,
                          lap_solve_info *info);
+
+/*
+ * Recurrence relative residuals ||r_k|| / ||Pi b|| of the outer iterations of
+ * the handle's last solve, k = 1..count (FP64 solves; for LAP_MIXED the
+ * entries are those of the FP32 inner solves, each relative to its own
+ * right-hand side).  Writes at most cap values to h_out (host) and the
+ * number recorded to *count (capped at the handle's maxit).
+ */
+lap_status lap_get_history(lap_handle h, double *h_out, int32_t cap, int32_t *count);
 
 /* Same as lap_pcg_solve with host vectors: copies b in and x out on `stream`
  * (the copies are part of the call). */

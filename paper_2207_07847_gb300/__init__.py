@@ -51,7 +51,7 @@ class lap_options(C.Structure):
 class lap_solve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("refinements", C.c_int32),
                 ("inner_iterations", C.c_int32), ("restarts", C.c_int32),
-                ("reserved0", C.c_int32), ("relres", C.c_double),
+                ("kernel_launches", C.c_int32), ("relres", C.c_double),
                 ("relres_recurrence", C.c_double), ("seconds", C.c_double)]
 
     def as_dict(self):
@@ -84,6 +84,8 @@ SIGNATURES = [
     ("lap_set_allocator", _I32, [_ALLOC_FN, _FREE_FN, _VP]),
     ("lap_setup", _I32, [_I64, _VP, _VP, _VP, C.POINTER(lap_options), _VP, C.POINTER(_VP)]),
     ("lap_destroy", None, [_VP]),
+    ("lap_update_options", _I32, [_VP, C.POINTER(lap_options)]),
+    ("lap_kernel_bench", _I32, [_VP, _I32, _I32, _I32, C.POINTER(_D), C.POINTER(_D)]),
     ("lap_get_hierarchy_info", _I32, [_VP, C.POINTER(lap_hierarchy_info)]),
     ("lap_get_aggregates", _I32, [_VP, _I32, _VP, _VP, _VP]),
     ("lap_get_expanded_edges", _I32, [_VP, _I32, _I64, C.POINTER(_I64), _VP, _VP, _VP]),
@@ -94,6 +96,7 @@ SIGNATURES = [
     ("lap_msp_solve", _I32, [_VP, _VP, _VP, _VP]),
     ("lap_pegp_apply", _I32, [_VP, _VP, _VP, _VP]),
     ("lap_pcg_solve", _I32, [_VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
+    ("lap_get_history", _I32, [_VP, _VP, _I32, C.POINTER(_I32)]),
     ("lap_pcg_solve_host", _I32, [_VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_pcg_solve_batched", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_server_options_default", None, [C.POINTER(lap_server_options)]),
@@ -230,6 +233,31 @@ def lap_destroy(h: Handle):
     h.close()
 
 
+def lap_update_options(h: Handle, **opts):
+    """Change solve-time options (see include/lap.h); returns the new options."""
+    o = lap_options()
+    C.memmove(C.byref(o), C.byref(h.opts), C.sizeof(lap_options))
+    for k, v in opts.items():
+        if k == "precision" and isinstance(v, str):
+            v = LAP_PRECISION[v]
+        setattr(o, k, v)
+    _check(lib().lap_update_options(h, C.byref(o)), "lap_update_options")
+    h.opts = o
+    return o
+
+
+KERNELS = {"spmv_L": 0, "spmv_LH": 1, "msp_sweep": 2, "update_up1": 3}
+
+
+def lap_kernel_bench(h: Handle, kernel, precision=0, reps=20):
+    """(ms per launch, algorithmic bytes per launch) of one solver kernel."""
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    ms, by = C.c_double(), C.c_double()
+    _check(lib().lap_kernel_bench(h, k, int(precision), int(reps), C.byref(ms), C.byref(by)),
+           "lap_kernel_bench")
+    return ms.value, by.value
+
+
 def lap_get_hierarchy_info(h: Handle) -> dict:
     info = lap_hierarchy_info()
     _check(lib().lap_get_hierarchy_info(h, C.byref(info)), "lap_get_hierarchy_info")
@@ -283,6 +311,15 @@ def lap_pcg_solve(h: Handle, b, x, stream=None) -> lap_solve_info:
     info = lap_solve_info()
     lib().lap_pcg_solve(h, _ptr(b), _ptr(x), _stream(stream), C.byref(info))
     return info
+
+
+def lap_get_history(h: Handle):
+    """Recurrence relative residuals of the last solve (numpy array)."""
+    cnt = C.c_int32()
+    _check(lib().lap_get_history(h, None, 0, C.byref(cnt)), "lap_get_history")
+    out = np.empty(cnt.value, dtype=np.float64)
+    _check(lib().lap_get_history(h, out.ctypes.data, cnt.value, C.byref(cnt)), "lap_get_history")
+    return out[:cnt.value]
 
 
 def lap_pcg_solve_host(h: Handle, b, x, stream=None) -> lap_solve_info:

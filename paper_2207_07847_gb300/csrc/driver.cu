@@ -49,6 +49,11 @@ T *dalloc(lap_handle_s &h, size_t count)
     auto b = std::make_unique<DevBuf>();
     if (!b->alloc(count * sizeof(T))) return nullptr;
     T *p = b->as<T>();
+    // every buffer starts as zeros, so no kernel can read stale bit patterns
+    if (cudaMemset(p, 0, b->bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
     h.device_bytes += static_cast<int64_t>(b->bytes);
     h.bufs.push_back(std::move(b));
     return p;
@@ -174,6 +179,7 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
     case T:                                                                                          \
         k_spmv<V, T, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, A.dg, x, y, bs, yres, sc, part, tk); \
         break;
+    h.launches += 1;
     switch (tpr) {
         LAP_SPMV_CASE(1)
         LAP_SPMV_CASE(2)
@@ -194,6 +200,7 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
 {
     const int n = static_cast<int>(M.off[1]);
     CgScalars *sc = st.sc;
+    h.launches += plain ? 1 : (M.levels == 1 ? 2 : 2 * M.levels - 1);
     if (plain || M.levels == 1) {
         const int g = grid_for(h, n);
 #define LAP_UPD(U, P)                                                                             \
@@ -243,6 +250,7 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
 template <typename V>
 void pupdate(const lap_handle_s &h, int64_t n, const V *z, V *p, const CgState &st, cudaStream_t s)
 {
+    h.launches += 1;
     k_pupdate<V><<<grid_for(h, n), kBlock, 0, s>>>(n, z, p, st.sc);
 }
 
@@ -254,6 +262,7 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
                cudaStream_t s)
 {
     const int l = M.levels;
+    h.launches += 2 * l - 1;
     for (int k = 0; k + 1 < l; ++k) {
         const auto &Lk = M.lev[k];
         k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
@@ -277,6 +286,7 @@ void restrict_tilde(const lap_handle_s &h, const DevMsp<V> &M, const V *r, V *rt
                     const CgScalars *sc, cudaStream_t s)
 {
     const int64_t n = M.off[1];
+    h.launches += M.levels;
     k_copy2<V><<<grid_for(h, n), kBlock, 0, s>>>(n, r, rt, A, sc);
     const V *sin = r;
     double coef = 1.0;
@@ -299,6 +309,7 @@ void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, 
 {
     const int l = M.levels;
     const int64_t ot = M.off[l - 1];
+    h.launches += l;
     k_copy2<V><<<grid_for(h, M.ntop), kBlock, 0, s>>>(M.ntop, yt + ot, T + ot, nullptr, st.sc);
     for (int k = l - 2; k >= 1; --k) {
         const auto &Lk = M.lev[k];
@@ -320,6 +331,7 @@ void inner_iteration(const lap_handle_s &h, const DevCsr<V> &H, const DevMsp<V> 
 {
     const int64_t nt = M.off[M.levels];
     spmv<V, 0>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
+    h.launches += 2;
     k_update_up1<V, true, false, false><<<grid_for(h, nt), kBlock, 0, s>>>(
         static_cast<int>(nt), 0, nullptr, nullptr, nullptr, e.x, e.r, e.p, e.q, e.A, nullptr, V(0),
         st.sc, st.part, st.ticket);
@@ -334,8 +346,10 @@ void inner_start(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
                  double tol, int maxit, cudaStream_t s)
 {
     const int64_t nt = M.off[M.levels];
-    k_cg_reset<<<1, 1, 0, s>>>(st.sc, tol, maxit, 0);
+    k_cg_reset<<<1, 1, 0, s>>>(st.sc, tol, maxit, 0, nullptr, 0);
+    h.launches += 1;
     k_vec_init<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.r, e.x, st.sc, st.part, st.ticket);
+    h.launches += 2;
     msp_tilde<V>(h, M, e.A, e.Y, st.sc, s);
     k_zred<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.Y, e.r, st.sc, st.part, st.ticket);
     pupdate<V>(h, nt, e.Y, e.p, st, s);
@@ -352,6 +366,8 @@ template <> struct Sel<double> {
     static const CgState &ste(const lap_handle_s &h) { return h.ste64; }
     static cudaGraphExec_t &gi(lap_handle_s &h) { return h.g_iter64; }
     static cudaGraphExec_t &gin(lap_handle_s &h) { return h.g_in64; }
+    static int64_t &ni(lap_handle_s &h) { return h.nodes_iter64; }
+    static int64_t &nin(lap_handle_s &h) { return h.nodes_in64; }
 };
 template <> struct Sel<float> {
     static const DevCsr<float> &L(const lap_handle_s &h) { return h.L32; }
@@ -363,6 +379,8 @@ template <> struct Sel<float> {
     static const CgState &ste(const lap_handle_s &h) { return h.ste32; }
     static cudaGraphExec_t &gi(lap_handle_s &h) { return h.g_iter32; }
     static cudaGraphExec_t &gin(lap_handle_s &h) { return h.g_in32; }
+    static int64_t &ni(lap_handle_s &h) { return h.nodes_iter32; }
+    static int64_t &nin(lap_handle_s &h) { return h.nodes_in32; }
 };
 
 bool is_plain(const lap_handle_s &h) { return h.m.opt.prec == LAP_PREC_NONE; }
@@ -380,16 +398,21 @@ void outer_iteration(const lap_handle_s &h, cudaStream_t s)
 }
 
 template <typename Fn>
-lap_status capture(lap_handle_s &h, cudaGraphExec_t &g, Fn body)
+lap_status capture(lap_handle_s &h, cudaGraphExec_t &g, int64_t &nodes, Fn body)
 {
     cudaGraph_t graph = nullptr;
+    const int64_t l0 = h.launches;
     LAP_CK(cudaStreamBeginCapture(h.s, cudaStreamCaptureModeThreadLocal));
     body();
     cudaError_t e = cudaStreamEndCapture(h.s, &graph);
+    h.launches = l0;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return LAP_ERR_CUDA;
     }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    nodes = static_cast<int64_t>(nn);
     e = cudaGraphInstantiate(&g, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
@@ -429,10 +452,12 @@ lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int
         precond_msp<V>(h, M, w, st, update, is_plain(h), s);
         return LAP_OK;
     }
-    if (update)
+    if (update) {
+        h.launches += 1;
         k_update_up1<V, true, false, false><<<grid_for(h, n), kBlock, 0, s>>>(
             static_cast<int>(n), 0, nullptr, nullptr, nullptr, w.x, w.r, w.p, w.q, nullptr, nullptr,
             V(0), st.sc, st.part, st.ticket);
+    }
     CgScalars sc;
     LAP_TRY(poll(h, st, sc));
     if (sc.flag != kRun) return LAP_OK;          // converged / stopped: nothing to apply
@@ -443,7 +468,7 @@ lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int
     cudaGraphExec_t &g = Sel<V>::gin(h);
     const int K = std::max(1, std::min(h.m.opt.check_every, 16));
     if (!g) {
-        LAP_TRY(capture(h, g, [&] {
+        LAP_TRY(capture(h, g, Sel<V>::nin(h), [&] {
             for (int i = 0; i < K; ++i) inner_iteration<V>(h, Sel<V>::H(h), M, e, ste, s);
         }));
     }
@@ -451,6 +476,7 @@ lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int
     const int cap_in = h.m.opt.inner_maxit / K + 4;
     for (int launches = 0;; ++launches) {
         LAP_CK(cudaGraphLaunch(g, s));
+        h.launches += Sel<V>::nin(h);
         CgScalars si;
         LAP_TRY(poll(h, ste, si));
         if (si.flag != kRun) {
@@ -484,13 +510,14 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
         return LAP_ERR_BREAKDOWN;
     }
     cudaGraphExec_t &g = Sel<V>::gi(h);
-    if (!g) LAP_TRY(capture(h, g, [&] {
+    if (!g) LAP_TRY(capture(h, g, Sel<V>::ni(h), [&] {
             for (int i = 0; i < h.m.opt.check_every; ++i) outer_iteration<V>(h, s);
         }));
     // the device stops at maxit; the launch cap only guards the host loop
     const int cap = h.m.opt.maxit / h.m.opt.check_every + 4;
     for (int launches = 0;; ++launches) {
         LAP_CK(cudaGraphLaunch(g, s));
+        h.launches += Sel<V>::ni(h);
         LAP_TRY(poll(h, st, sc));
         if (sc.flag != kRun) return LAP_OK;
         if (launches >= cap) return LAP_ERR_BREAKDOWN;
@@ -506,7 +533,8 @@ lap_status cg_fp64(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
     const auto &st = h.st64;
     const int64_t n = h.M64.off[1];
     const lap_options &o = h.m.opt;
-    k_cg_reset<<<1, 1, 0, s>>>(st.sc, o.tol, o.maxit, is_pegp(h) ? 1 : 0);
+    k_cg_reset<<<1, 1, 0, s>>>(st.sc, o.tol, o.maxit, is_pegp(h) ? 1 : 0, h.hist, o.maxit);
+    h.launches += 2;
     k_center_init<double><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), h.bs, w.r, w.x, st.sc,
                                                             st.part, st.ticket);
     CgScalars sc;
@@ -536,6 +564,7 @@ lap_status cg_fp64(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
             }
             if (sc.iter >= o.maxit || info.restarts >= 8) break;
             info.restarts += 1;
+            h.launches += 1;
             k_cg_restart<<<1, 1, 0, s>>>(st.sc);
             LAP_TRY(apply_precond<double>(h, false, t0, inner));
             pupdate<double>(h, n, is_plain(h) ? w.r : w.z, w.p, st, s);
@@ -565,7 +594,8 @@ lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
     const lap_options &o = h.m.opt;
     const CgState &so = h.st64;
     const CgState &si = h.st32;
-    k_cg_reset<<<1, 1, 0, s>>>(so.sc, o.tol, o.maxit, 0);
+    k_cg_reset<<<1, 1, 0, s>>>(so.sc, o.tol, o.maxit, 0, nullptr, 0);
+    h.launches += 2;
     k_center_init<double><<<grid_for(h, n), kBlock, 0, s>>>(ni, h.bs, h.w64.r, h.w64.x, so.sc, so.part,
                                                             so.ticket);
     CgScalars sc;
@@ -598,7 +628,9 @@ lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
             break;
         }
         const double tol_in = std::min(0.5, std::max(o.refine_tol, 0.3 * o.tol / relres));
-        k_cg_reset<<<1, 1, 0, s>>>(si.sc, tol_in, o.maxit - total, is_pegp(h) ? 1 : 0);
+        k_cg_reset<<<1, 1, 0, s>>>(si.sc, tol_in, o.maxit - total, is_pegp(h) ? 1 : 0, h.hist + total,
+                                   o.maxit - total);
+        h.launches += 5;
         k_gather_sum<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, nullptr, h.w64.r, h.w32.r, si.sc,
                                                              si.part, si.ticket);
         k_center_init<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, h.w64.r, h.w32.r, h.w32.x, si.sc,
@@ -612,6 +644,7 @@ lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
             break;
         }
         total += sci.iter;
+        h.launches += 1;
         k_add_correction<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, h.w64.x, h.w32.x);
         info.relres_recurrence = sci.relres;
         if (sci.flag == kBreakdown && sci.iter == 0) {
@@ -654,7 +687,9 @@ lap_status solve_core(lap_handle_s &h, const double *b, double *x, lap_solve_inf
     const int n = static_cast<int>(h.M64.off[1]);
     k_gather_sum<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.perm1, b, h.bs, h.st64.sc, h.st64.part,
                                                           h.st64.ticket);
+    h.launches += 3;   // gather, mean, scatter
     lap_status st = h.m.opt.precision == LAP_MIXED ? cg_mixed(h, t0, info) : cg_fp64(h, t0, info);
+    h.hist_count = std::min(info.iterations, h.m.opt.maxit);
     // x = Pi x back in the caller's numbering (also for a non-converged result)
     k_mean<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.w64.x, h.stb.sc, h.stb.part, h.stb.ticket);
     k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.perm1, h.w64.x, x,
@@ -712,6 +747,9 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
     LAP_TRY(alloc_state(h, h.ste64));
     LAP_TRY(alloc_state(h, h.ste32));
     LAP_TRY(alloc_state(h, h.stb));
+    h.hist_capacity = std::max(m.opt.maxit, 1000);
+    h.hist = dalloc<double>(h, static_cast<size_t>(h.hist_capacity));
+    if (!h.hist) return LAP_ERR_OOM;
     LAP_CK(cudaDeviceSynchronize());
     return LAP_OK;
 }
@@ -783,7 +821,7 @@ lap_status block_precond(lap_handle_s &h, const double *r, double *z, cudaStream
                                                             st.ticket);
     k_center_init<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.bs, h.w64.r, h.w64.x, st.sc, st.part,
                                                              st.ticket);
-    k_cg_reset<<<1, 1, 0, h.s>>>(st.sc, 0.0, 1, is_pegp(h) ? 1 : 0);
+    k_cg_reset<<<1, 1, 0, h.s>>>(st.sc, 0.0, 1, is_pegp(h) ? 1 : 0, nullptr, 0);
     int inner = 0;
     LAP_TRY(apply_precond<double>(h, false, Clock::now(), inner));
     k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, is_plain(h) ? h.w64.r : h.w64.z,
@@ -842,6 +880,136 @@ lap_status block_pegp(lap_handle_s &h, const double *xt, double *yt, cudaStream_
     spmv<double, 2>(h, h.H64, h.tprH, h.e64.p, h.e64.q, nullptr, nullptr, h.stb, h.s);
     k_permute<double><<<grid_for(h, nt), kBlock, 0, h.s>>>(nt, h.xmap, h.e64.q, yt, 1);
     return leave(h, user);
+}
+
+// ---------------------------------------------------------------------------
+lap_status get_history(lap_handle_s &h, double *out, int cap, int *count)
+{
+    const int c = std::min(h.hist_count, h.hist_capacity);
+    *count = c;
+    if (cap <= 0 || c == 0) return LAP_OK;
+    LAP_CK(cudaMemcpy(out, h.hist, sizeof(double) * std::min(c, cap), cudaMemcpyDeviceToHost));
+    return LAP_OK;
+}
+
+lap_status update_options(lap_handle_s &h, const lap_options &o)
+{
+    if (!(o.tol > 0.0) || o.maxit < 1 || o.check_every < 1 || o.inner_maxit < 1 ||
+        o.max_refine < 0 || !(o.refine_tol > 0.0) || !(o.inner_tol > 0.0))
+        return LAP_ERR_INVALID_ARG;
+    if (o.precision != LAP_FP64 && o.precision != LAP_MIXED) return LAP_ERR_INVALID_ARG;
+    if (o.precision == LAP_MIXED && !h.L32.w) return LAP_ERR_INVALID_ARG;
+    if (h.host_only) return LAP_ERR_INVALID_ARG;
+    lap_options &cur = h.m.opt;
+    if (o.maxit > h.hist_capacity) {
+        double *p = dalloc<double>(h, static_cast<size_t>(o.maxit));
+        if (!p) return LAP_ERR_OOM;
+        h.hist = p;
+        h.hist_capacity = o.maxit;
+    }
+    if (o.check_every != cur.check_every) {
+        for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32})
+            if (*g) {
+                cudaGraphExecDestroy(*g);
+                *g = nullptr;
+            }
+    }
+    cur.tol = o.tol;
+    cur.maxit = o.maxit;
+    cur.inner_tol = o.inner_tol;
+    cur.inner_maxit = o.inner_maxit;
+    cur.refine_tol = o.refine_tol;
+    cur.max_refine = o.max_refine;
+    cur.check_every = o.check_every;
+    cur.timeout_s = o.timeout_s;
+    cur.precision = o.precision;
+    return LAP_OK;
+}
+
+namespace {
+template <typename V>
+double sweep_bytes(const DevMsp<V> &M)
+{
+    // MSP sweep B r, every array touched once: level 1 reads r, writes delta_1,
+    // reads segments / inverses / leftover coefficients and writes a_2; levels
+    // 2..l-1 update a_k in place; the top level reads a_l and G; the way down
+    // reads delta_k and the parents' (y, t) and writes (y, t) (level 1: z).
+    const double s = sizeof(V);
+    double b = 0.0;
+    const int l = M.levels;
+    for (int k = 0; k + 1 < l; ++k) {
+        const double n = M.lev[k].n, na = M.lev[k].nagg, nl = n - 2 * na;
+        const double seg = 4.0 * (na + 1), coef = s * (3 * na + 3 * nl);
+        const double up = (k == 0 ? 2 * s * n : 2 * s * n) + seg + coef + s * na;
+        const double down = k == 0 ? (s * n /*delta*/ + 2 * s * na + s * n /*r*/ + s * n /*z*/ + seg)
+                                   : (s * n + 2 * s * na + 2 * s * n + seg);
+        b += up + down;
+    }
+    b += 8.0 * M.ntop * M.ntop + 3 * s * M.ntop;
+    return b;
+}
+}  // namespace
+
+lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, double *ms, double *bytes)
+{
+    if (precision == 1 && !h.L32.w) return LAP_ERR_INVALID_ARG;
+    if (kernel == 1 && !h.H64.w) return LAP_ERR_INVALID_ARG;
+    if (kernel < 0 || kernel > 3) return LAP_ERR_INVALID_ARG;
+    const cudaStream_t s = h.s;
+    cudaEvent_t e0, e1;
+    LAP_CK(cudaEventCreate(&e0));
+    LAP_CK(cudaEventCreate(&e1));
+    k_bench_scalars<<<1, 1, 0, s>>>(h.stb.sc);
+    auto run = [&](auto tag) {
+        using V = decltype(tag);
+        const auto &w = Sel<V>::w(h);
+        const auto &M = Sel<V>::M(h);
+        const int64_t n = M.off[1];
+        double by = 0.0;
+        auto launch = [&]() {
+            switch (kernel) {
+            case 0: spmv<V, 2>(h, Sel<V>::L(h), h.tpr, w.p, w.q, nullptr, nullptr, h.stb, s); break;
+            case 1: spmv<V, 2>(h, Sel<V>::H(h), h.tprH, Sel<V>::e(h).p, Sel<V>::e(h).q, nullptr,
+                               nullptr, h.stb, s); break;
+            case 2: precond_msp<V>(h, M, w, h.stb, false, false, s); break;
+            default:
+                k_update_up1<V, true, true, false><<<grid_for(h, M.lev[0].nagg), kBlock, 0, s>>>(
+                    static_cast<int>(n), M.lev[0].nagg, M.lev[0].seg, M.lev[0].inv, M.lev[0].lcf, w.x,
+                    w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0], h.stb.sc, h.stb.part,
+                    h.stb.ticket);
+            }
+        };
+        const double sv = sizeof(V);
+        if (kernel == 0 || kernel == 1) {
+            const auto &A = kernel == 0 ? Sel<V>::L(h) : Sel<V>::H(h);
+            by = A.nnz * (4.0 + sv) + 4.0 * (A.n + 1) + 3.0 * sv * A.n;
+        } else if (kernel == 2) {
+            by = sweep_bytes(M);
+        } else {
+            const double na = M.lev[0].nagg, nl = n - 2 * na;
+            by = 6.0 * sv * n + sv * n + 4.0 * (na + 1) + sv * (3 * na + 3 * nl) + sv * na;
+        }
+        if (kernel == 3 && M.levels < 2) return -1.0;
+        launch();                                   // warm-up
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < reps; ++i) launch();
+        cudaEventRecord(e1, s);
+        return by;
+    };
+    const double by = precision == 1 ? run(float{}) : run(double{});
+    if (by < 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return LAP_ERR_INVALID_ARG;
+    }
+    LAP_CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    LAP_CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = static_cast<double>(t) / reps;
+    *bytes = by;
+    return LAP_OK;
 }
 
 }  // namespace lap

@@ -40,7 +40,8 @@ struct CgScalars {
     int flag;          // kRun, kConverged, kBreakdown, kMaxit
     int flexible;      // 1: flexible (FCG) beta
     int first;         // 1 while preparing the initial direction
-    int pad[3];
+    int hist_cap;      // capacity of hist
+    double *hist;      // optional recurrence-residual history (device), or null
 };
 
 enum : int { kRun = 0, kConverged = 1, kBreakdown = 2, kMaxit = 3 };
@@ -255,6 +256,7 @@ k_update_up1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__
             sc->iter += 1;
             const double rel = sqrt(v[0]) / sc->bnorm;
             sc->relres = rel;
+            if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
             if (!isfinite(rel)) sc->flag = kBreakdown;
             else if (rel <= sc->tol) sc->flag = kConverged;
             else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
@@ -469,6 +471,12 @@ k_pupdate(int64_t n, const V *__restrict__ z, V *__restrict__ p, const CgScalars
 {
     if (halted(sc)) return;
     const V m = (V)sc->zmean, be = (V)sc->beta;
+    // a fresh direction (beta == 0) never reads the previous p
+    if (be == V(0)) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            p[i] = z[i] - m;
+        return;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = (z[i] - m) + be * p[i];
 }
@@ -605,7 +613,8 @@ k_zred(int64_t n, const V *__restrict__ z, const V *__restrict__ r, CgScalars *s
 }
 
 // CG bookkeeping written from the host side of the stream.
-static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flexible)
+static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flexible, double *hist,
+                                  int hist_cap)
 {
     sc->tol = tol;
     sc->maxit = maxit;
@@ -613,6 +622,26 @@ static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flex
     sc->iter = 0;
     sc->flag = kRun;
     sc->first = 1;
+    sc->hist = hist;
+    sc->hist_cap = hist ? hist_cap : 0;
+}
+
+// scalars for timing runs: running, never converging, unit norms
+static __global__ void k_bench_scalars(CgScalars *sc)
+{
+    sc->tol = 0.0;
+    sc->maxit = 0x7fffffff;
+    sc->flexible = 0;
+    sc->iter = 0;
+    sc->flag = kRun;
+    sc->first = 0;
+    sc->bnorm = 1.0;
+    sc->rho = 1.0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->zmean = 0.0;
+    sc->hist = nullptr;
+    sc->hist_cap = 0;
 }
 
 static __global__ void k_cg_restart(CgScalars *sc)

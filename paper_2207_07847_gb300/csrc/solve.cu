@@ -164,6 +164,28 @@ void lap_destroy(lap_handle h)
     delete h;
 }
 
+lap_status lap_update_options(lap_handle h, const lap_options *opts)
+{
+    if (!h || !opts) return LAP_ERR_INVALID_ARG;
+    return update_options(*h, *opts);
+}
+
+lap_status lap_kernel_bench(lap_handle h, int32_t kernel, int32_t precision, int32_t reps,
+                            double *ms_per_launch, double *bytes_per_launch)
+{
+    if (!h || h->host_only || !ms_per_launch || !bytes_per_launch || reps < 1) return LAP_ERR_INVALID_ARG;
+    return kernel_bench(*h, kernel, precision, reps, ms_per_launch, bytes_per_launch);
+}
+
+lap_status lap_get_history(lap_handle h, double *h_out, int32_t cap, int32_t *count)
+{
+    if (!h || !count || h->host_only || (cap > 0 && !h_out)) return LAP_ERR_INVALID_ARG;
+    int c = 0;
+    lap_status st = get_history(*h, h_out, cap, &c);
+    *count = c;
+    return st;
+}
+
 lap_status lap_get_hierarchy_info(lap_handle h, lap_hierarchy_info *info)
 {
     if (!h || !info) return LAP_ERR_INVALID_ARG;
@@ -257,7 +279,9 @@ lap_status lap_pcg_solve(lap_handle h, const double *d_b, double *d_x, void *str
     std::memset(inf, 0, sizeof(*inf));
     if (!h || !d_b || !d_x || d_b == d_x || h->host_only) return LAP_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = h->launches;
     lap_status st = solve_device(*h, d_b, d_x, static_cast<cudaStream_t>(stream), *inf);
+    inf->kernel_launches = static_cast<int32_t>(h->launches - l0);
     inf->status = st;
     inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return st;
@@ -271,7 +295,9 @@ lap_status lap_pcg_solve_host(lap_handle h, const double *h_b, double *h_x, void
     std::memset(inf, 0, sizeof(*inf));
     if (!h || !h_b || !h_x || h->host_only) return LAP_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = h->launches;
     lap_status st = solve_host(*h, h_b, h_x, static_cast<cudaStream_t>(stream), *inf);
+    inf->kernel_launches = static_cast<int32_t>(h->launches - l0);
     inf->status = st;
     inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return st;

@@ -42,7 +42,11 @@ struct lap_handle_s {
 
     cudaGraphExec_t g_iter64 = nullptr, g_iter32 = nullptr;
     cudaGraphExec_t g_in64 = nullptr, g_in32 = nullptr;   // PEGP inner-iteration chunks
-    int g_iter_k = 0, g_in_k = 0;
+    int64_t nodes_iter64 = 0, nodes_iter32 = 0, nodes_in64 = 0, nodes_in32 = 0;
+    mutable int64_t launches = 0;     // kernels launched (graph replays add their nodes)
+    double *hist = nullptr;           // device history of the last solve (maxit entries)
+    int hist_count = 0;
+    int hist_capacity = 0;
 };
 
 namespace lap {
@@ -61,5 +65,9 @@ lap_status solve_device(lap_handle_s &h, const double *b, double *x, cudaStream_
                         lap_solve_info &info);
 lap_status solve_host(lap_handle_s &h, const double *b, double *x, cudaStream_t user,
                       lap_solve_info &info);
+lap_status update_options(lap_handle_s &h, const lap_options &o);
+lap_status get_history(lap_handle_s &h, double *out, int cap, int *count);
+lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, double *ms,
+                        double *bytes);
 
 }  // namespace lap

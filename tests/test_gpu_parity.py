@@ -6,9 +6,12 @@ tensors and compares with the oracle on the same seeded inputs.  Tolerances:
 * single operator applications in FP64 (L x, P(mu)^T r, P(mu) y, L_H x, the MSP
   and PEGP preconditioners): the difference is rounding of sums taken in
   another order, bounded by a few ulps of the magnitudes summed;
-* FP64 solves: iteration counts within +-1 of the oracle's and the two
-  solutions agree in the residual norm, ||L (x_gpu - x_oracle)|| <= 1e-9 ||Pi b||,
-  with both true relative residuals <= 1e-8;
+* FP64 solves: the recurrence residual histories agree to 1e-9 relative over
+  the first 25 iterations (the same iteration, step by step, before rounding
+  differences of the two summation orders grow); iteration counts agree to
+  +-1, or to 3% for runs of more than 400 iterations on badly conditioned
+  problems, where CG's loss of orthogonality amplifies rounding; both true
+  relative residuals are <= 1e-8, so ||L (x_gpu - x_oracle)|| <= 2e-8 ||Pi b||;
 * mixed precision: true relative residual <= 1e-8 and the solution within the
   error that residual allows of the oracle's.
 """
@@ -154,6 +157,16 @@ def _oracle_solve(g, b, kind, mu, **kw):
     return oracle.solve(g, b, kind, mu=mu, seed=17, **kw)
 
 
+def _check_trajectory(h, info, ref, head=25):
+    hist = P.lap_get_history(h)
+    oh = np.array(ref.history)
+    m = min(head, len(hist), len(oh))
+    assert len(hist) == info.iterations
+    np.testing.assert_allclose(hist[:m], oh[:m], rtol=1e-9)
+    band = 1 if max(info.iterations, ref.iters) <= 400 else max(1, int(0.03 * ref.iters))
+    assert abs(info.iterations - ref.iters) <= band, (info.iterations, ref.iters)
+
+
 @pytest.mark.parametrize("kind", ["msp", "none"])
 def test_fp64_solve_parity(case, kind):
     name, g, ho, ops = case
@@ -162,11 +175,11 @@ def test_fp64_solve_parity(case, kind):
     x, info = solve_gpu(h, dev(b))
     ref = _oracle_solve(g, b, kind, 0.8, maxit=3000)
     assert info.status == 0 and ref.converged
-    assert abs(info.iterations - ref.iters) <= 1, (info.iterations, ref.iters)
+    _check_trajectory(h, info, ref)
     xg = host(x)
     bp = b - b.mean()
     assert np.linalg.norm(bp - ops.L @ xg) <= 1e-8 * np.linalg.norm(bp)
-    assert np.linalg.norm(ops.L @ (xg - ref.x)) <= 1e-9 * np.linalg.norm(bp)
+    assert np.linalg.norm(ops.L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
     assert abs(xg.mean()) <= 1e-12 * np.abs(xg).max()
     assert info.relres <= 1e-8
 
@@ -176,14 +189,17 @@ def test_fp64_pegp_inner_parity():
     b = gg.rhs(g.n, seed=8)
     h = P.lap_setup(g, seed=17, mu=0.8, prec="pegp_inner", inner_tol=1e-6, inner_maxit=500)
     x, info = solve_gpu(h, dev(b))
-    ref = _oracle_solve(g, b, "pegp_inner", 0.8, inner_tol=1e-6, inner_maxit=500)
+    M = oracle.make_preconditioner("pegp_inner", g, mu=0.8, seed=17, inner_tol=1e-6,
+                                   inner_maxit=500)
+    ref = oracle.pcg(M.ops.L, b, M, flexible=True)
     assert info.status == 0 and ref.converged
-    assert abs(info.iterations - ref.iters) <= 1
+    _check_trajectory(h, info, ref, head=10)
+    assert abs(info.inner_iterations - sum(M.inner_iters)) <= max(2, 0.02 * sum(M.inner_iters))
     L = laplacian(g.adjacency())
     bp = b - b.mean()
     xg = host(x)
     assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
-    assert np.linalg.norm(L @ (xg - ref.x)) <= 1e-9 * np.linalg.norm(bp)
+    assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
 
 
 @pytest.mark.parametrize("kind", ["msp", "pegp_inner"])
@@ -230,14 +246,15 @@ def test_single_level_graph_is_solved_directly():
 def test_ragged_path_and_ring_sizes(n):
     for g in (gg.path(n, w=np.linspace(1, 2, n - 1)), gg.ring(max(n, 5), 2, weights="uniform", seed=n)):
         b = gg.rhs(g.n, seed=n)
-        h = P.lap_setup(g, seed=3, coarse_max=2, maxit=5000)
+        h = P.lap_setup(g, seed=17, coarse_max=2, maxit=5000)
         x, info = solve_gpu(h, dev(b))
         ref = _oracle_solve(g, b, "msp", 0.8, coarse_max=2, maxit=5000)
         assert info.status == 0 and ref.converged
-        assert abs(info.iterations - ref.iters) <= 1
+        _check_trajectory(h, info, ref)
         L = laplacian(g.adjacency())
         bp = b - b.mean()
-        assert np.linalg.norm(L @ (host(x) - ref.x)) <= 1e-9 * np.linalg.norm(bp)
+        assert np.linalg.norm(bp - L @ host(x)) <= 1e-8 * np.linalg.norm(bp)
+        assert np.linalg.norm(L @ (host(x) - ref.x)) <= 2e-8 * np.linalg.norm(bp)
 
 
 def test_solves_are_deterministic_and_stream_safe():
@@ -255,6 +272,19 @@ def test_solves_are_deterministic_and_stream_safe():
     xh = np.empty(g.n)
     i3 = P.lap_pcg_solve_host(h, host(b), xh)
     assert i3.status == 0 and np.array_equal(xh, host(x1))
+
+
+def test_tight_tolerance_solutions_agree():
+    """Solved to 1e-11 the two solutions agree in the residual norm to 1e-10."""
+    g = SMALL["grid2d_64"]()
+    b = gg.rhs(g.n, seed=21)
+    h = P.lap_setup(g, seed=17, mu=0.8, tol=1e-11)
+    x, info = solve_gpu(h, dev(b))
+    ref = _oracle_solve(g, b, "msp", 0.8, tol=1e-11)
+    assert info.status == 0 and ref.converged
+    L = laplacian(g.adjacency())
+    bp = b - b.mean()
+    assert np.linalg.norm(L @ (host(x) - ref.x)) <= 1e-10 * np.linalg.norm(bp)
 
 
 def test_maxit_reports_no_convergence():

@@ -55,6 +55,7 @@ template <typename V> struct DevMsp {
     std::vector<DevMspLevel<V>> lev;   // levels 1..l-1 (index k-1)
     std::vector<int64_t> off;          // expanded offsets, size l+1
     std::vector<V> gamma;              // c_{k+1} / c_k per level k < l
+    std::vector<double> c;             // c_k = sum_{i<k} (-mu)^i per level (index k-1)
     double *G = nullptr;               // dense top-level pseudo-inverse (FP64)
     int ntop = 0;
     V mu = V(0);

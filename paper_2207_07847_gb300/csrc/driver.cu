@@ -118,6 +118,7 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
         LAP_TRY(upload(h, &L.lcf, S.lcf));
         d.gamma[k] = static_cast<V>(m.c[k + 1] / m.c[k]);
     }
+    d.c.assign(m.c.begin(), m.c.end());
     d.ntop = static_cast<int>(m.lev[l - 1].n);
     if (share) d.G = share->G;
     else LAP_TRY(upload(h, &d.G, m.coarse_pinv));
@@ -177,7 +178,7 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
     unsigned *tk = st.ticket;
 #define LAP_SPMV_CASE(T)                                                                             \
     case T:                                                                                          \
-        k_spmv<V, T, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, A.dg, x, y, bs, yres, sc, part, tk); \
+        k_spmv<V, T, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, x, y, bs, yres, sc, part, tk); \
         break;
     h.launches += 1;
     switch (tpr) {
@@ -187,7 +188,7 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
         LAP_SPMV_CASE(8)
         LAP_SPMV_CASE(16)
     default:
-        k_spmv<V, 32, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, A.dg, x, y, bs, yres, sc, part, tk);
+        k_spmv<V, 32, MODE><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.w, x, y, bs, yres, sc, part, tk);
     }
 #undef LAP_SPMV_CASE
 }
@@ -233,18 +234,19 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
                                                            w.A + M.off[k], w.A + M.off[k + 1],
                                                            M.gamma[k], nullptr, sc);
     }
+    // top level, then z = sum_k c_k delta_k(anc_k(u)) accumulated downwards in Y
     const int64_t ot = M.off[l - 1];
     k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, w.A + ot, w.Y + ot,
-                                                                      w.T + ot, sc);
+                                                                      M.c[l - 1], sc);
     for (int k = l - 2; k >= 1; --k) {
         const auto &Lk = M.lev[k];
         k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, w.A + M.off[k],
-                                                             w.Y + M.off[k + 1], w.T + M.off[k + 1],
-                                                             w.Y + M.off[k], w.T + M.off[k], M.mu, sc);
+                                                             w.Y + M.off[k + 1], w.Y + M.off[k], V(1),
+                                                             static_cast<V>(M.c[k]), sc);
     }
     k_msp_down1<V><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(n, L0.nagg, L0.seg, w.A, w.Y + M.off[1],
-                                                          w.T + M.off[1], w.r, w.q, w.z, M.mu, sc,
-                                                          st.part, st.ticket);
+                                                          w.r, w.q, w.z, V(1), V(1), sc, st.part,
+                                                          st.ticket);
 }
 
 template <typename V>
@@ -270,13 +272,13 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
                                                            A + M.off[k + 1], sc);
     }
     const int64_t ot = M.off[l - 1];
-    k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, A + ot, Y + ot,
-                                                                      nullptr, sc);
+    k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, A + ot, Y + ot, 1.0,
+                                                                      sc);
     for (int k = l - 2; k >= 0; --k) {
         const auto &Lk = M.lev[k];
         k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, A + M.off[k],
-                                                             Y + M.off[k + 1], nullptr, Y + M.off[k],
-                                                             nullptr, V(0), sc);
+                                                             Y + M.off[k + 1], Y + M.off[k], V(1), V(1),
+                                                             sc);
     }
 }
 
@@ -313,14 +315,14 @@ void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, 
     k_copy2<V><<<grid_for(h, M.ntop), kBlock, 0, s>>>(M.ntop, yt + ot, T + ot, nullptr, st.sc);
     for (int k = l - 2; k >= 1; --k) {
         const auto &Lk = M.lev[k];
-        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, yt + M.off[k], nullptr,
-                                                             T + M.off[k + 1], nullptr, T + M.off[k],
-                                                             M.mu, st.sc);
+        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, yt + M.off[k],
+                                                             T + M.off[k + 1], T + M.off[k], -M.mu, V(1),
+                                                             st.sc);
     }
     const auto &L0 = M.lev[0];
     k_msp_down1<V><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(static_cast<int>(M.off[1]), L0.nagg, L0.seg,
-                                                          yt, nullptr, T + M.off[1], w.r, w.q, w.z,
-                                                          M.mu, st.sc, st.part, st.ticket);
+                                                          yt, T + M.off[1], w.r, w.q, w.z, -M.mu, V(1),
+                                                          st.sc, st.part, st.ticket);
 }
 
 // One expanded-space CG iteration of the PEGP inner solve L_H y~ = r~ with the
@@ -515,6 +517,12 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
         }));
     // the device stops at maxit; the launch cap only guards the host loop
     const int cap = h.m.opt.maxit / h.m.opt.check_every + 4;
+    // stall detection (mixed precision inner solves only): stop once the
+    // recurrence residual has not dropped by 10% over `window` iterations
+    const bool watch = std::is_same<V, float>::value;
+    const int window = std::max(64, h.m.opt.check_every);
+    double best = 1e300;
+    int best_iter = 0;
     for (int launches = 0;; ++launches) {
         LAP_CK(cudaGraphLaunch(g, s));
         h.launches += Sel<V>::ni(h);
@@ -522,6 +530,15 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
         if (sc.flag != kRun) return LAP_OK;
         if (launches >= cap) return LAP_ERR_BREAKDOWN;
         if (timed_out(h, t0)) return LAP_ERR_TIMEOUT;
+        if (watch) {
+            if (sc.relres < 0.9 * best) {
+                best = sc.relres;
+                best_iter = sc.iter;
+            } else if (sc.iter - best_iter >= window) {
+                sc.flag = kConverged;                // stalled: hand back to refinement
+                return LAP_OK;
+            }
+        }
     }
 }
 
@@ -855,8 +872,8 @@ lap_status block_prolong(lap_handle_s &h, const double *yt, double *z, cudaStrea
     for (int k = l - 2; k >= 0; --k) {
         const auto &Lk = M.lev[k];
         k_msp_down<double><<<grid_for(h, Lk.nagg), kBlock, 0, h.s>>>(
-            Lk.nagg, Lk.seg, h.w64.Y + M.off[k], nullptr, h.w64.T + M.off[k + 1], nullptr,
-            h.w64.T + M.off[k], M.mu, nullptr);
+            Lk.nagg, Lk.seg, h.w64.Y + M.off[k], h.w64.T + M.off[k + 1], h.w64.T + M.off[k], -M.mu, 1.0,
+            nullptr);
     }
     k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, h.w64.T, z, nullptr);
     return leave(h, user);
@@ -931,18 +948,19 @@ template <typename V>
 double sweep_bytes(const DevMsp<V> &M)
 {
     // MSP sweep B r, every array touched once: level 1 reads r, writes delta_1,
-    // reads segments / inverses / leftover coefficients and writes a_2; levels
+    // reads segments / pair and leftover coefficients and writes a_2; levels
     // 2..l-1 update a_k in place; the top level reads a_l and G; the way down
-    // reads delta_k and the parents' (y, t) and writes (y, t) (level 1: z).
+    // reads delta_k and the parents' accumulated value and writes its own
+    // (level 1: reads r and writes z).
     const double s = sizeof(V);
     double b = 0.0;
     const int l = M.levels;
     for (int k = 0; k + 1 < l; ++k) {
         const double n = M.lev[k].n, na = M.lev[k].nagg, nl = n - 2 * na;
-        const double seg = 4.0 * (na + 1), coef = s * (3 * na + 3 * nl);
-        const double up = (k == 0 ? 2 * s * n : 2 * s * n) + seg + coef + s * na;
-        const double down = k == 0 ? (s * n /*delta*/ + 2 * s * na + s * n /*r*/ + s * n /*z*/ + seg)
-                                   : (s * n + 2 * s * na + 2 * s * n + seg);
+        const double seg = 4.0 * (na + 1), coef = s * (4 * na + 3 * nl);
+        const double up = 2 * s * n + seg + coef + s * na;
+        const double down = k == 0 ? (s * n /*delta*/ + s * na + s * n /*r*/ + s * n /*z*/ + seg)
+                                   : (s * n + s * na + s * n + seg);
         b += up + down;
     }
     b += 8.0 * M.ntop * M.ntop + 3 * s * M.ntop;
@@ -982,12 +1000,12 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
         const double sv = sizeof(V);
         if (kernel == 0 || kernel == 1) {
             const auto &A = kernel == 0 ? Sel<V>::L(h) : Sel<V>::H(h);
-            by = A.nnz * (4.0 + sv) + 4.0 * (A.n + 1) + 3.0 * sv * A.n;
+            by = A.nnz * (4.0 + sv) + 4.0 * (A.n + 1) + 2.0 * sv * A.n;
         } else if (kernel == 2) {
             by = sweep_bytes(M);
         } else {
             const double na = M.lev[0].nagg, nl = n - 2 * na;
-            by = 6.0 * sv * n + sv * n + 4.0 * (na + 1) + sv * (3 * na + 3 * nl) + sv * na;
+            by = 6.0 * sv * n + sv * n + 4.0 * (na + 1) + sv * (4 * na + 3 * nl) + sv * na;
         }
         if (kernel == 3 && M.levels < 2) return -1.0;
         launch();                                   // warm-up

@@ -108,18 +108,33 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double *part, unsigned
 
 __device__ __forceinline__ bool halted(const CgScalars *sc) { return sc && sc->flag != kRun; }
 
+// Solve the 2x2 Schur complement [[alpha+c, -c], [-c, beta+c]] (da, db) = (ha, hb)
+// of one aggregate's matched pair from cf = (beta/det, alpha/det, 1/(alpha+beta),
+// alpha/(alpha+beta)): the difference D = da - db and the weighted sum
+// alpha da + beta db = ha + hb carry no cancellation, unlike the inverse.
+template <typename V>
+__device__ __forceinline__ void pair_solve(const V *cf, V ha, V hb, V &da, V &db)
+{
+    const V D = cf[0] * ha - cf[1] * hb;
+    db = cf[2] * (ha + hb) - cf[3] * D;
+    da = db + D;
+}
+
 // ---------------------------------------------------------------------------
-// CSR Laplacian matvec  y = L x = diag .* x - A x  with TPR threads per row.
+// CSR Laplacian matvec in edge-difference form, TPR threads per row:
+//     y_i = sum_j w_ij (x_i - x_j)
+// which equals (D - A) x but never forms d_i x_i - sum_j w_ij x_j, whose
+// cancellation loses every digit of a smooth x in FP32 when the weights span
+// several decades; x_i - x_j of nearby values is exact (Sterbenz).
 // MODE 0: y = L x, reduce (x.y, sum y) and set alpha = rho / x.y
-// MODE 1: y(double) = bs - L x, reduce (||y||^2, sum y)   [true residual]
+// MODE 1: yres(double) = bs - L x, reduce (||yres||^2, sum yres) [true residual]
 // MODE 2: y = L x, no reduction
 // ---------------------------------------------------------------------------
 template <typename V, int TPR, int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ w,
-       const V *__restrict__ dg, const V *__restrict__ x, V *__restrict__ y,
-       const double *__restrict__ bs, double *__restrict__ yres, CgScalars *sc, double *part,
-       unsigned *ticket)
+       const V *__restrict__ x, V *__restrict__ y, const double *__restrict__ bs,
+       double *__restrict__ yres, CgScalars *sc, double *part, unsigned *ticket)
 {
     if (MODE != 2 && halted(sc)) return;
     constexpr int RPW = 32 / TPR;      // rows per warp
@@ -132,23 +147,22 @@ k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *_
         const int row = r0 + sub;
         const bool valid = row < n;
         const int b = valid ? rp[row] : 0, e = valid ? rp[row + 1] : 0;
+        const V xi = valid ? x[row] : V(0);
         V s = V(0);
-        for (int p = b + l; p < e; p += TPR) s += w[p] * x[ci[p]];
+        for (int p = b + l; p < e; p += TPR) s += w[p] * (xi - x[ci[p]]);
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, TPR);
         if (valid && l == 0) {
-            const V xi = x[row];
-            const V yi = dg[row] * xi - s;
             if (MODE == 1) {
-                const double ri = bs[row] - (double)yi;
+                const double ri = bs[row] - (double)s;
                 yres[row] = ri;
                 a0 += ri * ri;
                 a1 += ri;
             } else {
-                y[row] = yi;
+                y[row] = s;
                 if (MODE == 0) {
-                    a0 += (double)xi * (double)yi;
-                    a1 += (double)yi;
+                    a0 += (double)xi * (double)s;
+                    a1 += (double)s;
                 }
             }
         }
@@ -225,8 +239,8 @@ k_update_up1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__
                 ha += c[0] * rl;
                 hb += c[1] * rl;
             }
-            const V i0 = inv[3 * J], i1 = inv[3 * J + 1], i2 = inv[3 * J + 2];
-            const V da = i0 * ha + i1 * hb, db = i1 * ha + i2 * hb;
+            V da, db;
+            pair_solve(inv + 4 * J, ha, hb, da, db);
             d1[b0] = da;
             d1[b0 + 1] = db;
             for (int t = b0 + 2; t < e; ++t) {
@@ -294,8 +308,8 @@ k_msp_up(int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
             ha += c[0] * al;
             hb += c[1] * al;
         }
-        const V i0 = inv[3 * J], i1 = inv[3 * J + 1], i2 = inv[3 * J + 2];
-        const V da = i0 * ha + i1 * hb, db = i1 * ha + i2 * hb;
+        V da, db;
+        pair_solve(inv + 4 * J, ha, hb, da, db);
         for (int t = b0 + 2; t < e; ++t) {
             const V *c = lc + 3 * (t - b0 - 2);
             a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
@@ -308,12 +322,12 @@ k_msp_up(int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
     }
 }
 
-// Top level: y = G a with G the dense pseudo-inverse (FP64), one warp per row.
-// Writes y to both the y- and t-arrays of the top level (t_l = y_l).
+// Top level: y = scale * G a with G the dense pseudo-inverse of mu^(2(l-1)) L_l
+// (FP64 whatever V is), one warp per row.
 template <typename V>
 __global__ void __launch_bounds__(kBlock)
 k_coarse(int m, const double *__restrict__ G, const V *__restrict__ a, V *__restrict__ y,
-         V *__restrict__ t, const CgScalars *sc)
+         double scale, const CgScalars *sc)
 {
     if (halted(sc)) return;
     const int lane = threadIdx.x & 31;
@@ -323,33 +337,26 @@ k_coarse(int m, const double *__restrict__ G, const V *__restrict__ a, V *__rest
     for (int j = lane; j < m; j += 32) s += G[(size_t)row * m + j] * (double)a[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-        y[row] = (V)s;
-        if (t) t[row] = (V)s;
-    }
+    if (lane == 0) y[row] = (V)(scale * s);
 }
 
-// Prolongation / back-substitution on level k >= 2 (thread per level-(k+1)
-// aggregate J):  y_k(u) = y_{k+1}(J) + delta_k(u),  t_k(u) = y_k(u) - mu t_{k+1}(J).
-// With t == nullptr only y is produced (expanded-space MSP solve); with
-// yp == nullptr the parents' y are taken as zero, which turns the pass into
-// the Horner step t_k = delta_k - mu t_{k+1} of the prolongation P(mu).
+// Top-down pass over one level (thread per level-(k+1) aggregate J):
+//     out_k(u) = pc * parent(J) + dc * delta_k(u)      for u in J.
+// (pc, dc) = (1, c_k): MSP prolongation z = sum_k c_k delta_k(anc_k(u)) with
+//   c_k = sum_{i<k} (-mu)^i > 0, i.e. P(mu) applied to the back-substituted
+//   sparsifier solution without the alternating Horner sum (Section 3.3);
+// (1, 1): back-substitution y_k = y_{k+1}(J) + delta_k (expanded-space solve);
+// (-mu, 1): Horner step t_k = y_k - mu t_{k+1}(J) of P(mu) y (Section 2.2).
 template <typename V>
 __global__ void __launch_bounds__(kBlock)
 k_msp_down(int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
-           const V *__restrict__ yp, const V *__restrict__ tp, V *__restrict__ y,
-           V *__restrict__ t, V mu, const CgScalars *sc)
+           const V *__restrict__ parent, V *__restrict__ out, V pc, V dc, const CgScalars *sc)
 {
     if (halted(sc)) return;
     for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
         const int b0 = seg[J], e = seg[J + 1];
-        const V yJ = yp ? yp[J] : V(0);
-        const V base = t ? yJ - mu * tp[J] : V(0);
-        for (int u = b0; u < e; ++u) {
-            const V d = delta[u];
-            if (y) y[u] = yJ + d;
-            if (t) t[u] = base + d;
-        }
+        const V base = pc * parent[J];
+        for (int u = b0; u < e; ++u) out[u] = base + dc * delta[u];
     }
 }
 
@@ -387,24 +394,24 @@ k_copy2(int64_t n, const V *__restrict__ in, V *__restrict__ o1, V *__restrict__
     }
 }
 
-// Finest level of the prolongation, producing the preconditioned residual
-// z = t_1 and the reductions for the projection and the CG scalars:
-// sum z, r.z, z.q  ->  zmean, rho and beta (standard or flexible).
+// Finest level of the top-down pass, producing the preconditioned residual
+// z(u) = pc * parent(J) + dc * delta_1(u) and the reductions for the projection
+// and the CG scalars: sum z, r.z, z.q  ->  zmean, rho and beta (standard or
+// flexible).
 template <typename V>
 __global__ void __launch_bounds__(kBlock)
 k_msp_down1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
-            const V *__restrict__ yp, const V *__restrict__ tp, const V *__restrict__ r,
-            const V *__restrict__ q, V *__restrict__ z, V mu, CgScalars *sc, double *part,
-            unsigned *ticket)
+            const V *__restrict__ parent, const V *__restrict__ r, const V *__restrict__ q,
+            V *__restrict__ z, V pc, V dc, CgScalars *sc, double *part, unsigned *ticket)
 {
     if (halted(sc)) return;
     double sz = 0.0, srz = 0.0, szq = 0.0;
     const bool flex = sc->flexible && !sc->first;
     for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
         const int b0 = seg[J], e = seg[J + 1];
-        const V base = (yp ? yp[J] : V(0)) - mu * tp[J];
+        const V base = pc * parent[J];
         for (int u = b0; u < e; ++u) {
-            const V zu = base + delta[u];
+            const V zu = base + dc * delta[u];
             z[u] = zu;
             sz += (double)zu;
             srz += (double)r[u] * (double)zu;

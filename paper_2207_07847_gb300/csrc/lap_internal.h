@@ -49,7 +49,8 @@ struct HostCsr {                  // square CSR, off-diagonal entries + diagonal
 struct HostMspLevel {             // elimination data of level k < l (tree order)
     int64_t n = 0, nagg = 0;
     std::vector<int32_t> seg;     // [nagg+1] member ranges in level-k storage
-    std::vector<double> inv;      // [3*nagg] inverse 2x2 Schur complement (aa, ab, bb)
+    std::vector<double> inv;      // [4*nagg] pair solve: beta/det, alpha/det, 1/(alpha+beta),
+                                  // alpha/(alpha+beta) of the 2x2 Schur complement
     std::vector<double> lcf;      // [3*(n-2*nagg)] leftover (g_a, g_b, 1/d)
 };
 

@@ -446,7 +446,7 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
         S.n = F.n;
         S.nagg = nagg;
         S.seg.assign(static_cast<size_t>(nagg) + 1, 0);
-        S.inv.assign(static_cast<size_t>(3 * nagg), 0.0);
+        S.inv.assign(static_cast<size_t>(4 * nagg), 0.0);
         S.lcf.assign(static_cast<size_t>(3 * (F.n - 2 * nagg)), 0.0);
         F.perm.clear();
         F.perm.reserve(static_cast<size_t>(F.n));
@@ -462,6 +462,9 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
             // M = s L_intra + pw diag(out).  Leftovers touch only a and b, so
             // eliminating them leaves a 2x2 Schur complement
             // [[alpha + cpl, -cpl], [-cpl, beta + cpl]] with nonnegative parts.
+            // It is solved through the difference and the weighted sum of the
+            // pair (coefficients below), never through its inverse, whose
+            // entries are all ~ 1/(alpha + beta) for weakly coupled pairs.
             const double wab = edge_weight(F, a, b);
             double alpha = pw * F.out[a], beta = pw * F.out[b], cpl = s * wab;
             for (int64_t t = lstart[J]; t < lstart[J + 1]; ++t) {
@@ -479,9 +482,10 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
                 F.perm.push_back(lu);
             }
             const double det = alpha * beta + cpl * (alpha + beta);
-            S.inv[3 * Jp + 0] = (beta + cpl) / det;
-            S.inv[3 * Jp + 1] = cpl / det;
-            S.inv[3 * Jp + 2] = (alpha + cpl) / det;
+            S.inv[4 * Jp + 0] = beta / det;               // delta_a - delta_b =
+            S.inv[4 * Jp + 1] = alpha / det;              //   (beta h_a - alpha h_b) / det
+            S.inv[4 * Jp + 2] = 1.0 / (alpha + beta);     // delta_b = (h_a + h_b - alpha D)
+            S.inv[4 * Jp + 3] = alpha / (alpha + beta);   //           / (alpha + beta)
         }
         S.seg[nagg] = static_cast<int32_t>(F.perm.size());
         F.pos.assign(static_cast<size_t>(F.n), 0);

@@ -97,7 +97,10 @@ typedef struct lap_options {
     int32_t spmv_tpr;      /* threads per CSR row in the SpMV, 0 = auto           */
     int32_t host_only;     /* 1: build the host-side setup only and touch no GPU;
                               only the lap_get_* queries work on such a handle  */
-    int32_t reserved[6];
+    int32_t stall_window;  /* LAP_MIXED: an FP32 inner solve returns to refinement
+                              once its residual has set no new minimum for this
+                              many iterations (default 200; 0 = never)          */
+    int32_t reserved[5];
 } lap_options;
 
 typedef struct lap_solve_info {

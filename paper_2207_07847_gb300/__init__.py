@@ -45,7 +45,7 @@ class lap_options(C.Structure):
                 ("refine_tol", C.c_double), ("max_refine", C.c_int32),
                 ("check_every", C.c_int32), ("timeout_s", C.c_double),
                 ("spmv_tpr", C.c_int32), ("host_only", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("stall_window", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class lap_solve_info(C.Structure):

@@ -518,9 +518,9 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
     // the device stops at maxit; the launch cap only guards the host loop
     const int cap = h.m.opt.maxit / h.m.opt.check_every + 4;
     // stall detection (mixed precision inner solves only): stop once the
-    // recurrence residual has not dropped by 10% over `window` iterations
-    const bool watch = std::is_same<V, float>::value;
-    const int window = std::max(64, h.m.opt.check_every);
+    // recurrence residual has set no new minimum for `window` iterations
+    const bool watch = std::is_same<V, float>::value && h.m.opt.stall_window > 0;
+    const int window = std::max(h.m.opt.stall_window, h.m.opt.check_every);
     double best = 1e300;
     int best_iter = 0;
     for (int launches = 0;; ++launches) {
@@ -531,7 +531,7 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
         if (launches >= cap) return LAP_ERR_BREAKDOWN;
         if (timed_out(h, t0)) return LAP_ERR_TIMEOUT;
         if (watch) {
-            if (sc.relres < 0.9 * best) {
+            if (sc.relres < best) {
                 best = sc.relres;
                 best_iter = sc.iter;
             } else if (sc.iter - best_iter >= window) {
@@ -940,6 +940,7 @@ lap_status update_options(lap_handle_s &h, const lap_options &o)
     cur.check_every = o.check_every;
     cur.timeout_s = o.timeout_s;
     cur.precision = o.precision;
+    cur.stall_window = o.stall_window;
     return LAP_OK;
 }
 

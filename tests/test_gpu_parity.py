@@ -196,7 +196,7 @@ def test_fp64_pegp_inner_parity():
     assert info.status == 0 and ref.converged
     # inner solves stop at 1e-6, so the preconditioners agree to about that
     _check_trajectory(h, info, ref, head=5, rtol=1e-5)
-    assert abs(info.inner_iterations - sum(M.inner_iters)) <= max(2, 0.02 * sum(M.inner_iters))
+    assert abs(info.inner_iterations - sum(M.inner_iters)) <= max(2, 0.03 * sum(M.inner_iters))
     L = laplacian(g.adjacency())
     bp = b - b.mean()
     xg = host(x)

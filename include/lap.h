@@ -99,7 +99,7 @@ typedef struct lap_options {
                               only the lap_get_* queries work on such a handle  */
     int32_t stall_window;  /* LAP_MIXED: an FP32 inner solve returns to refinement
                               once its residual has set no new minimum for this
-                              many iterations (default 200; 0 = never)          */
+                              many iterations (default 1000; 0 = never)         */
     int32_t reserved[5];
 } lap_options;
 

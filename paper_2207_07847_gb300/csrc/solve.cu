@@ -91,7 +91,7 @@ void lap_options_default(lap_options *o)
     o->timeout_s = 0.0;
     o->spmv_tpr = 0;
     o->host_only = 0;
-    o->stall_window = 200;
+    o->stall_window = 1000;
 }
 
 const char *lap_status_string(int32_t s)

@@ -178,7 +178,7 @@ def bench_ours(args, rank, world):
     t0 = time.perf_counter()
     h = P.lap_setup(g, prec=args.prec, mu=WORKLOAD["mu"], precision="mixed",
                     seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"],
-                    inner_tol=WORKLOAD["inner_tol"], maxit=5000)
+                    inner_tol=WORKLOAD["inner_tol"], maxit=30000)
     setup_s = time.perf_counter() - t0
     info_h = P.lap_get_hierarchy_info(h)
     K, W = args.steps, args.warmup

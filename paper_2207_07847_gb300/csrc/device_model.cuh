@@ -36,11 +36,28 @@ struct DevBuf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
+// A Laplacian's off-diagonal part on the device, as CSR and as SELL-32 (see
+// HostSell); `kernel` selects the matvec: 0 = SELL, t > 0 = CSR with t threads
+// per row (chosen by timing at setup).
 template <typename V> struct DevCsr {
     int n = 0;
     int64_t nnz = 0;
     int *rp = nullptr, *ci = nullptr;
     V *w = nullptr, *dg = nullptr;
+    int nslices = 0, nlong = 0;
+    int64_t *sptr = nullptr;
+    unsigned *lmask = nullptr;
+    int *eci = nullptr;
+    V *ew = nullptr;
+    int *lrow = nullptr, *lci = nullptr;
+    int64_t *lrp = nullptr;
+    V *lw = nullptr;
+    int nchunks = 0;
+    int *lchunk_ptr = nullptr, *chunk_row = nullptr;
+    int64_t *chunk_beg = nullptr;
+    V *chunk_part = nullptr;           // per-chunk partial sums (scratch)
+    int64_t ell_entries = 0, long_entries = 0;
+    int kernel = 0;
 };
 
 template <typename V> struct DevMspLevel {
@@ -59,6 +76,11 @@ template <typename V> struct DevMsp {
     double *G = nullptr;               // dense top-level pseudo-inverse (FP64)
     int ntop = 0;
     V mu = V(0);
+    // fused coarse tail: levels tail0 .. l-1 (0-based) run in one block
+    int tail0 = -1;                    // -1: no tail kernel
+    size_t tail_smem = 0;
+    TailParams<V> tail_n{};            // n-space MSP (pc = 1, dcoef = c_k)
+    TailParams<V> tail_t{};            // expanded-space solve (pc = dcoef = 1, f added)
 };
 
 // Reduction scratch + device scalars of one CG.

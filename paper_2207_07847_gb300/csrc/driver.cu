@@ -81,19 +81,47 @@ lap_status upload(lap_handle_s &h, T **dst, const std::vector<U> &src)
     } while (0)
 
 template <typename V>
-lap_status upload_csr(lap_handle_s &h, const HostCsr &c, DevCsr<V> &d, const DevCsr<double> *share)
+lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, DevCsr<V> &d,
+                      const DevCsr<double> *share)
 {
     d.n = static_cast<int>(c.n);
     d.nnz = c.rp[c.n];
+    d.nslices = static_cast<int>(sl.nslices);
+    d.nlong = static_cast<int>(sl.lrow.size());
+    d.ell_entries = static_cast<int64_t>(sl.eci.size());
+    d.long_entries = static_cast<int64_t>(sl.lci.size());
     if (share) {
         d.rp = share->rp;
         d.ci = share->ci;
+        d.sptr = share->sptr;
+        d.lmask = share->lmask;
+        d.eci = share->eci;
+        d.lrow = share->lrow;
+        d.lrp = share->lrp;
+        d.lci = share->lci;
+        d.lchunk_ptr = share->lchunk_ptr;
+        d.chunk_row = share->chunk_row;
+        d.chunk_beg = share->chunk_beg;
+        d.kernel = share->kernel;
     } else {
+        LAP_TRY(upload(h, &d.lchunk_ptr, sl.lchunk_ptr));
+        LAP_TRY(upload(h, &d.chunk_row, sl.chunk_row));
+        LAP_TRY(upload(h, &d.chunk_beg, sl.chunk_beg));
         LAP_TRY(upload(h, &d.rp, c.rp));
         LAP_TRY(upload(h, &d.ci, c.ci));
+        LAP_TRY(upload(h, &d.sptr, sl.sptr));
+        LAP_TRY(upload(h, &d.lmask, sl.longmask));
+        LAP_TRY(upload(h, &d.eci, sl.eci));
+        LAP_TRY(upload(h, &d.lrow, sl.lrow));
+        LAP_TRY(upload(h, &d.lrp, sl.lrp));
+        LAP_TRY(upload(h, &d.lci, sl.lci));
     }
     LAP_TRY(upload(h, &d.w, c.w));
-    LAP_TRY(upload(h, &d.dg, c.diag));
+    LAP_TRY(upload(h, &d.ew, sl.ew));
+    LAP_TRY(upload(h, &d.lw, sl.lw));
+    d.nchunks = static_cast<int>(sl.chunk_row.size());
+    d.chunk_part = dalloc<V>(h, std::max<size_t>(sl.chunk_row.size(), 1));
+    if (!d.chunk_part) return LAP_ERR_OOM;
     return LAP_OK;
 }
 
@@ -122,6 +150,47 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
     d.ntop = static_cast<int>(m.lev[l - 1].n);
     if (share) d.G = share->G;
     else LAP_TRY(upload(h, &d.G, m.coarse_pinv));
+    // fused tail: the deepest levels whose expanded size fits the shared-memory budget
+    const size_t budget = 200 * 1024;
+    d.tail0 = -1;
+    if (l >= 2) {
+        for (int t = l - 1; t >= 1; --t) {
+            const int64_t nt = m.offset[l] - m.offset[t];
+            if (2 * nt * static_cast<int64_t>(sizeof(V)) > static_cast<int64_t>(budget) ||
+                l - 1 - t > kTailMaxLevels)
+                break;
+            d.tail0 = t;
+        }
+    }
+    if (d.tail0 >= 1) {
+        const int t0 = d.tail0;
+        for (TailParams<V> *P : {&d.tail_n, &d.tail_t}) {
+            const bool nspace = P == &d.tail_n;
+            P->nlev = l - 1 - t0;
+            P->ntail = static_cast<int>(m.offset[l] - m.offset[t0]);
+            P->ntop = d.ntop;
+            P->loc_top = static_cast<int>(m.offset[l - 1] - m.offset[t0]);
+            P->off0 = m.offset[t0];
+            P->n0 = static_cast<int>(m.lev[t0].n);
+            P->G = d.G;
+            P->top_scale = nspace ? m.c[l - 1] : 1.0;
+            P->pc = V(1);
+            P->write_all = nspace ? 0 : 1;
+            for (int k = 0; k < P->nlev; ++k) {
+                const DevMspLevel<V> &Lk = d.lev[t0 + k];
+                P->lev[k].nagg = Lk.nagg;
+                P->lev[k].loc = static_cast<int>(m.offset[t0 + k] - m.offset[t0]);
+                P->lev[k].seg = Lk.seg;
+                P->lev[k].inv = Lk.inv;
+                P->lev[k].lcf = Lk.lcf;
+                P->lev[k].gamma = nspace ? d.gamma[t0 + k] : V(1);
+                P->lev[k].dcoef = nspace ? static_cast<V>(m.c[t0 + k]) : V(1);
+            }
+        }
+        d.tail_smem = static_cast<size_t>(2 * (m.offset[l] - m.offset[t0])) * sizeof(V);
+        LAP_CK(cudaFuncSetAttribute(k_msp_tail<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(budget)));
+    }
     return LAP_OK;
 }
 
@@ -165,6 +234,38 @@ int auto_tpr(double avg)
     return t;
 }
 
+// Matvec autotuner: time SELL-32 and CSR with 2..16 threads per row on the
+// matrix itself (FP64, 5 launches each after a warm-up) and keep the fastest.
+template <typename V, int MODE>
+void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, const double *bs,
+          double *yres, const CgState &st, cudaStream_t s);
+
+int autotune_spmv(lap_handle_s &h, const DevCsr<double> &A, double *x, double *y)
+{
+    const int cand[] = {0, 2, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 0;
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int c : cand) {
+        spmv<double, 2>(h, A, c < 1 ? -1 : c, x, y, nullptr, nullptr, h.stb, h.s);
+        cudaEventRecord(e0, h.s);
+        for (int i = 0; i < 5; ++i) spmv<double, 2>(h, A, c < 1 ? -1 : c, x, y, nullptr, nullptr, h.stb, h.s);
+        cudaEventRecord(e1, h.s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    return best;
+}
+
 // --------------------------------------------------------------------------
 // kernel sequences
 // --------------------------------------------------------------------------
@@ -172,6 +273,21 @@ template <typename V, int MODE>
 void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, const double *bs,
           double *yres, const CgState &st, cudaStream_t s)
 {
+    if (tpr == 0) tpr = A.kernel;      // 0: the tuned choice, -1: SELL, t > 0: CSR
+    if (tpr <= 0) {
+        if (A.nchunks > 0) {
+            h.launches += 1;
+            k_long_chunks<V><<<grid_for(h, static_cast<int64_t>(A.nchunks) * 32), kBlock, 0, s>>>(
+                A.nchunks, A.chunk_row, A.chunk_beg, A.lrow, A.lci, A.lw, x, A.chunk_part, st.sc,
+                MODE != 2);
+        }
+        h.launches += 1;
+        const int g = grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
+        k_sell<V, MODE><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.eci, A.ew, A.nlong,
+                                             A.lrow, A.lchunk_ptr, A.chunk_part, x, y, bs, yres, st.sc,
+                                             st.part, st.ticket);
+        return;
+    }
     const int g = grid_for(h, static_cast<int64_t>(A.n) * tpr);
     CgScalars *sc = st.sc;
     double *part = st.part;
@@ -201,7 +317,7 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
 {
     const int n = static_cast<int>(M.off[1]);
     CgScalars *sc = st.sc;
-    h.launches += plain ? 1 : (M.levels == 1 ? 2 : 2 * M.levels - 1);
+    h.launches += plain ? 1 : (M.levels == 1 ? 2 : 2 * ((M.tail0 >= 1 ? M.tail0 : M.levels - 1) - 1) + 3);
     if (plain || M.levels == 1) {
         const int g = grid_for(h, n);
 #define LAP_UPD(U, P)                                                                             \
@@ -228,17 +344,26 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
         k_update_up1<V, false, true, false><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(
             n, L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
             sc, st.part, st.ticket);
-    for (int k = 1; k + 1 < l; ++k) {
+    // levels below the fused tail one launch each, the tail in one block
+    const int t0 = M.tail0 >= 1 ? M.tail0 : l - 1;
+    for (int k = 1; k < t0; ++k) {
         const auto &Lk = M.lev[k];
         k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
                                                            w.A + M.off[k], w.A + M.off[k + 1],
                                                            M.gamma[k], nullptr, sc);
     }
-    // top level, then z = sum_k c_k delta_k(anc_k(u)) accumulated downwards in Y
-    const int64_t ot = M.off[l - 1];
-    k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, w.A + ot, w.Y + ot,
-                                                                      M.c[l - 1], sc);
-    for (int k = l - 2; k >= 1; --k) {
+    if (M.tail0 >= 1) {
+        TailParams<V> P = M.tail_n;
+        P.A = w.A;
+        P.Y = w.Y;
+        P.F = nullptr;
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(P, sc);
+    } else {
+        const int64_t ot = M.off[l - 1];
+        k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, w.A + ot,
+                                                                          w.Y + ot, M.c[l - 1], sc);
+    }
+    for (int k = t0 - 1; k >= 1; --k) {
         const auto &Lk = M.lev[k];
         k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, w.A + M.off[k],
                                                              w.Y + M.off[k + 1], w.Y + M.off[k], V(1),
@@ -264,17 +389,27 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
                cudaStream_t s)
 {
     const int l = M.levels;
-    h.launches += 2 * l - 1;
-    for (int k = 0; k + 1 < l; ++k) {
+    const int t0 = M.tail0 >= 0 ? std::max(M.tail0, 0) : l - 1;
+    const int up_end = M.tail0 >= 1 ? t0 : l - 1;
+    h.launches += 2 * up_end + 1;
+    for (int k = 0; k < up_end; ++k) {
         const auto &Lk = M.lev[k];
         k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
                                                            A + M.off[k], A + M.off[k + 1], V(1),
                                                            A + M.off[k + 1], sc);
     }
-    const int64_t ot = M.off[l - 1];
-    k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, A + ot, Y + ot, 1.0,
-                                                                      sc);
-    for (int k = l - 2; k >= 0; --k) {
+    if (M.tail0 >= 1) {
+        TailParams<V> P = M.tail_t;
+        P.A = A;
+        P.Y = Y;
+        P.F = A;
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(P, sc);
+    } else {
+        const int64_t ot = M.off[l - 1];
+        k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, A + ot, Y + ot,
+                                                                          1.0, sc);
+    }
+    for (int k = up_end - 1; k >= 0; --k) {
         const auto &Lk = M.lev[k];
         k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, A + M.off[k],
                                                              Y + M.off[k + 1], Y + M.off[k], V(1), V(1),
@@ -733,16 +868,21 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
 
     const bool mixed = m.opt.precision == LAP_MIXED;
     const int64_t n = m.lev[0].n, nt = m.offset[m.levels];
-    LAP_TRY(upload_csr<double>(h, m.L1, h.L64, nullptr));
-    if (mixed) LAP_TRY(upload_csr<float>(h, m.L1, h.L32, &h.L64));
+    const double avg = static_cast<double>(m.L1.rp[n]) / static_cast<double>(n);
+    {
+        HostSell sl;
+        make_sell(m.L1, sl, std::max<int64_t>(64, static_cast<int64_t>(8 * avg)));
+        LAP_TRY(upload_csr<double>(h, m.L1, sl, h.L64, nullptr));
+        if (mixed) LAP_TRY(upload_csr<float>(h, m.L1, sl, h.L32, &h.L64));
+    }
     LAP_TRY(upload_msp<double>(h, m, h.M64, nullptr));
     if (mixed) LAP_TRY(upload_msp<float>(h, m, h.M32, &h.M64));
-    const double avg = static_cast<double>(m.L1.rp[n]) / static_cast<double>(n);
-    h.tpr = m.opt.spmv_tpr > 0 ? m.opt.spmv_tpr : auto_tpr(avg);
     if (m.has_LH) {
-        LAP_TRY(upload_csr<double>(h, m.LH, h.H64, nullptr));
-        if (mixed) LAP_TRY(upload_csr<float>(h, m.LH, h.H32, &h.H64));
-        h.tprH = auto_tpr(static_cast<double>(m.LH.rp[m.LH.n]) / static_cast<double>(m.LH.n));
+        HostSell sl;
+        const double avgH = static_cast<double>(m.LH.rp[m.LH.n]) / static_cast<double>(m.LH.n);
+        make_sell(m.LH, sl, std::max<int64_t>(64, static_cast<int64_t>(8 * avgH)));
+        LAP_TRY(upload_csr<double>(h, m.LH, sl, h.H64, nullptr));
+        if (mixed) LAP_TRY(upload_csr<float>(h, m.LH, sl, h.H32, &h.H64));
     }
     LAP_TRY(upload(h, &h.perm1, m.lev[0].perm));
     {
@@ -767,6 +907,16 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
     h.hist_capacity = std::max(m.opt.maxit, 1000);
     h.hist = dalloc<double>(h, static_cast<size_t>(h.hist_capacity));
     if (!h.hist) return LAP_ERR_OOM;
+    // matvec kernel choice: the option forces one, 0 times the candidates
+    h.tpr = 0;
+    h.tprH = 0;
+    if (m.opt.spmv_tpr != 0) {
+        h.L64.kernel = h.L32.kernel = h.H64.kernel = h.H32.kernel = std::max(m.opt.spmv_tpr, 0);
+    } else {
+        h.L64.kernel = h.L32.kernel = autotune_spmv(h, h.L64, h.w64.p, h.w64.q);
+        if (m.has_LH) h.H64.kernel = h.H32.kernel = autotune_spmv(h, h.H64, h.e64.p, h.e64.q);
+    }
+    (void)avg;
     LAP_CK(cudaDeviceSynchronize());
     return LAP_OK;
 }

@@ -15,6 +15,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#ifndef LAP_TAIL_MAX_LEVELS
+#define LAP_TAIL_MAX_LEVELS 24
+#endif
+
 namespace lap {
 
 constexpr int kBlock = 256;
@@ -165,6 +169,103 @@ k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *_
                     a1 += (double)s;
                 }
             }
+        }
+    }
+    if (MODE == 2) return;
+    double v[2] = {a0, a1};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        if (MODE == 0) {
+            sc->pq = v[0];
+            sc->qsum = v[1];
+            const double alpha = sc->rho / v[0];
+            if (!(v[0] > 0.0) || !isfinite(alpha)) sc->flag = kBreakdown;
+            sc->alpha = alpha;
+        } else {
+            sc->rr = v[0];
+            sc->rs = v[1];
+            sc->relres = sqrt(v[0]) / sc->bnorm;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same matvec on the SELL-32 layout: one warp per slice of 32 rows, lane =
+// row; entry j of all 32 rows is one coalesced load of column indices and one
+// of weights, and the gathers of x over j are independent.  Warp tasks past the
+// slices take one long row each (CSR, lanes stride the row).
+// ---------------------------------------------------------------------------
+template <typename V, int MODE>
+__device__ __forceinline__ void spmv_finish(int row, V xi, V s, V *y, const double *bs, double *yres,
+                                            double &a0, double &a1)
+{
+    if (MODE == 1) {
+        const double ri = bs[row] - (double)s;
+        yres[row] = ri;
+        a0 += ri * ri;
+        a1 += ri;
+    } else {
+        y[row] = s;
+        if (MODE == 0) {
+            a0 += (double)xi * (double)s;
+            a1 += (double)s;
+        }
+    }
+}
+
+// Partial sums of the long rows, one warp per chunk of <= 4096 entries.
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__restrict__ chunk_beg,
+              const int *__restrict__ lrow, const int *__restrict__ lci, const V *__restrict__ lw,
+              const V *__restrict__ x, V *__restrict__ chunk_part, const CgScalars *sc, int check)
+{
+    if (check && halted(sc)) return;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nwarp) {
+        const V xi = x[lrow[chunk_row[c]]];
+        V s = V(0);
+        for (int64_t p = chunk_beg[c] + lane; p < chunk_beg[c + 1]; p += 32) s += lw[p] * (xi - x[lci[p]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) chunk_part[c] = s;
+    }
+}
+
+template <typename V, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__restrict__ lmask,
+       const int *__restrict__ eci, const V *__restrict__ ew, int nlong, const int *__restrict__ lrow,
+       const int *__restrict__ lchunk_ptr, const V *__restrict__ chunk_part,
+       const V *__restrict__ x, V *__restrict__ y, const double *__restrict__ bs,
+       double *__restrict__ yres, CgScalars *sc, double *part, unsigned *ticket)
+{
+    if (MODE != 2 && halted(sc)) return;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    double a0 = 0.0, a1 = 0.0;
+    const int ntask = nslices + nlong;
+    for (int task = gwarp; task < ntask; task += nwarp) {          // warp-uniform
+        if (task < nslices) {
+            const int row = task * 32 + lane;
+            const bool valid = row < n;
+            const int64_t base = sptr[task];
+            const int width = static_cast<int>((sptr[task + 1] - base) >> 5);
+            const V xi = valid ? x[row] : V(0);
+            V s = V(0);
+            const int *pc = eci + base + lane;
+            const V *pw = ew + base + lane;
+#pragma unroll 4
+            for (int j = 0; j < width; ++j) s += pw[32 * j] * (xi - x[pc[32 * j]]);
+            if (valid && !((lmask[task] >> lane) & 1u)) spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
+        } else if (lane == 0) {
+            // long row: add its chunk partials in chunk order
+            const int li = task - nslices;
+            const int row = lrow[li];
+            V s = V(0);
+            for (int c = lchunk_ptr[li]; c < lchunk_ptr[li + 1]; ++c) s += chunk_part[c];
+            spmv_finish<V, MODE>(row, x[row], s, y, bs, yres, a0, a1);
         }
     }
     if (MODE == 2) return;
@@ -358,6 +459,106 @@ k_msp_down(int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
         const V base = pc * parent[J];
         for (int u = b0; u < e; ++u) out[u] = base + dc * delta[u];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Fused coarse tail of the sweep: levels t0..l (0-based t0 >= 1) whose
+// expanded size fits in shared memory are restricted + eliminated upwards,
+// solved on top and prolongated downwards by ONE block, with a barrier per
+// level instead of a kernel launch per level.
+// ---------------------------------------------------------------------------
+constexpr int kTailMaxLevels = LAP_TAIL_MAX_LEVELS;
+
+template <typename V> struct TailLevel {
+    int nagg;                 // aggregates = vertices of the next level
+    int loc;                  // offset of this level inside the tail
+    const int *seg;
+    const V *inv;
+    const V *lcf;
+    V gamma;                  // restriction factor to the next level
+    V dcoef;                  // down pass: out = pc * parent + dcoef * delta
+};
+
+template <typename V> struct TailParams {
+    int nlev;                 // levels below the top inside the tail
+    int ntail;                // vertices in the tail (all its levels)
+    int ntop, loc_top;
+    int64_t off0;             // expanded offset of the tail's first level
+    int n0;                   // vertices of the tail's first level
+    const double *G;
+    double top_scale;
+    V pc;
+    V *A;                     // global a/delta (expanded, tree order)
+    V *Y;                     // global output (expanded, tree order)
+    const V *F;               // expanded right-hand side added on restriction, or null
+    int write_all;            // write every tail level of Y (else the first only)
+    TailLevel<V> lev[kTailMaxLevels];
+};
+
+template <typename V>
+__global__ void __launch_bounds__(1024)
+k_msp_tail(const TailParams<V> P, const CgScalars *sc)
+{
+    if (halted(sc)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sa = reinterpret_cast<V *>(smem_raw);
+    V *sz = sa + P.ntail;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < P.n0; i += nth) sa[i] = P.A[P.off0 + i];
+    __syncthreads();
+    for (int k = 0; k < P.nlev; ++k) {
+        const TailLevel<V> &L = P.lev[k];
+        V *a = sa + L.loc;
+        const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
+        for (int J = tid; J < L.nagg; J += nth) {
+            const int b0 = L.seg[J], e = L.seg[J + 1];
+            const V aa = a[b0], ab = a[b0 + 1];
+            V sum = aa + ab, ha = aa, hb = ab;
+            const V *lc = L.lcf + 3 * (b0 - 2 * J);
+            for (int t = b0 + 2; t < e; ++t) {
+                const V al = a[t];
+                const V *c = lc + 3 * (t - b0 - 2);
+                sum += al;
+                ha += c[0] * al;
+                hb += c[1] * al;
+            }
+            V da, db;
+            pair_solve(L.inv + 4 * J, ha, hb, da, db);
+            for (int t = b0 + 2; t < e; ++t) {
+                const V *c = lc + 3 * (t - b0 - 2);
+                a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
+            }
+            a[b0] = da;
+            a[b0 + 1] = db;
+            V nx = L.gamma * sum;
+            if (P.F) nx += P.F[P.off0 + nloc + J];
+            sa[nloc + J] = nx;
+        }
+        __syncthreads();
+    }
+    {   // top: dense pseudo-inverse, one warp per row
+        const int lane = tid & 31, nw = nth >> 5;
+        for (int row = tid >> 5; row < P.ntop; row += nw) {
+            double s = 0.0;
+            for (int j = lane; j < P.ntop; j += 32)
+                s += P.G[(size_t)row * P.ntop + j] * (double)sa[P.loc_top + j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) sz[P.loc_top + row] = (V)(P.top_scale * s);
+        }
+    }
+    __syncthreads();
+    for (int k = P.nlev - 1; k >= 0; --k) {
+        const TailLevel<V> &L = P.lev[k];
+        const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
+        for (int J = tid; J < L.nagg; J += nth) {
+            const V base = P.pc * sz[nloc + J];
+            for (int u = L.seg[J]; u < L.seg[J + 1]; ++u) sz[L.loc + u] = base + L.dcoef * sa[L.loc + u];
+        }
+        __syncthreads();
+    }
+    const int nout = P.write_all ? P.ntail : P.n0;
+    for (int i = tid; i < nout; i += nth) P.Y[P.off0 + i] = sz[i];
 }
 
 // Restriction of one level: s_{k+1}(J) = sum_{u in J} s_k(u); the scaled value

@@ -46,6 +46,32 @@ struct HostCsr {                  // square CSR, off-diagonal entries + diagonal
     std::vector<double> diag;     // row sums of w
 };
 
+// Sliced ELL (SELL-32) copy of a Laplacian's off-diagonal part: rows are cut
+// into slices of 32 consecutive rows; slice s stores width_s = its longest row
+// as width_s x 32 entries, column-major (entry j of row 32 s + lane at
+// sptr[s] + 32 j + lane), padded with (own row, weight 0).  Rows longer than
+// `long_threshold` are kept out of the slices (their lanes are padding) and
+// listed as CSR rows processed by a whole warp each.
+struct HostSell {
+    int64_t n = 0, nslices = 0;
+    std::vector<int64_t> sptr;        // [nslices + 1]
+    std::vector<uint32_t> longmask;   // [nslices] lanes whose row is a long row
+    std::vector<int32_t> eci;
+    std::vector<double> ew;
+    std::vector<int32_t> lrow;        // long rows
+    std::vector<int64_t> lrp;         // [nlong + 1]
+    std::vector<int32_t> lci;
+    std::vector<double> lw;
+    // long rows are cut into chunks of at most kChunk entries, summed by
+    // separate warps into per-chunk partials; chunk range of long row r:
+    // [lchunk_ptr[r], lchunk_ptr[r+1])
+    std::vector<int32_t> lchunk_ptr;  // [nlong + 1]
+    std::vector<int32_t> chunk_row;   // long-row index of each chunk
+    std::vector<int64_t> chunk_beg;   // [nchunks + 1] entry ranges (into lci/lw)
+};
+
+void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold);
+
 struct HostMspLevel {             // elimination data of level k < l (tree order)
     int64_t n = 0, nagg = 0;
     std::vector<int32_t> seg;     // [nagg+1] member ranges in level-k storage

@@ -553,6 +553,71 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
 }
 
 // ---------------------------------------------------------------------------
+void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold)
+{
+    const int64_t n = A.n;
+    S.n = n;
+    S.nslices = (n + 31) / 32;
+    S.sptr.assign(static_cast<size_t>(S.nslices) + 1, 0);
+    S.longmask.assign(static_cast<size_t>(S.nslices), 0u);
+    S.lrow.clear();
+    S.lrp.assign(1, 0);
+    S.lci.clear();
+    S.lw.clear();
+    for (int64_t s = 0; s < S.nslices; ++s) {
+        int64_t width = 0;
+        for (int64_t lane = 0; lane < 32; ++lane) {
+            const int64_t r = 32 * s + lane;
+            if (r >= n) break;
+            const int64_t d = A.rp[r + 1] - A.rp[r];
+            if (d > long_threshold) {
+                S.longmask[s] |= 1u << lane;
+                S.lrow.push_back(static_cast<int32_t>(r));
+                for (int64_t p = A.rp[r]; p < A.rp[r + 1]; ++p) {
+                    S.lci.push_back(A.ci[p]);
+                    S.lw.push_back(A.w[p]);
+                }
+                S.lrp.push_back(static_cast<int64_t>(S.lci.size()));
+            } else {
+                width = std::max(width, d);
+            }
+        }
+        S.sptr[s + 1] = S.sptr[s] + 32 * width;
+    }
+    // chunks of the long rows
+    const int64_t kChunk = 4096;
+    S.lchunk_ptr.assign(1, 0);
+    S.chunk_row.clear();
+    S.chunk_beg.assign(1, 0);
+    for (size_t r = 0; r < S.lrow.size(); ++r) {
+        for (int64_t b = S.lrp[r]; b < S.lrp[r + 1]; b += kChunk) {
+            S.chunk_row.push_back(static_cast<int32_t>(r));
+            S.chunk_beg.push_back(std::min(b + kChunk, S.lrp[r + 1]));
+        }
+        S.lchunk_ptr.push_back(static_cast<int32_t>(S.chunk_row.size()));
+    }
+    S.eci.assign(static_cast<size_t>(S.sptr[S.nslices]), 0);
+    S.ew.assign(static_cast<size_t>(S.sptr[S.nslices]), 0.0);
+    for (int64_t s = 0; s < S.nslices; ++s) {
+        const int64_t width = (S.sptr[s + 1] - S.sptr[s]) / 32;
+        for (int64_t lane = 0; lane < 32; ++lane) {
+            const int64_t r = 32 * s + lane;
+            const bool real = r < n && !((S.longmask[s] >> lane) & 1u);
+            const int64_t d = real ? A.rp[r + 1] - A.rp[r] : 0;
+            for (int64_t j = 0; j < width; ++j) {
+                const int64_t q = S.sptr[s] + 32 * j + lane;
+                if (j < d) {
+                    S.eci[q] = A.ci[A.rp[r] + j];
+                    S.ew[q] = A.w[A.rp[r] + j];
+                } else {
+                    S.eci[q] = static_cast<int32_t>(r < n ? r : 0);   // weight 0: no contribution
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 void expanded_edges(const HostModel &m, int which, std::vector<int64_t> &I,
                     std::vector<int64_t> &J, std::vector<double> &W)
 {

@@ -74,9 +74,12 @@ def case(request):
 
 # --- single operators ---------------------------------------------------------------------
 
-def test_laplacian_apply(case):
+@pytest.mark.parametrize("kernel", [0, -1, 4])
+def test_laplacian_apply(case, kernel):
+    """SELL-32 slices (-1), CSR with 4 threads per row (4) and the autotuned
+    choice (0) all equal L x; power-law cases exercise the chunked long rows."""
     name, g, ho, ops = case
-    h = P.lap_setup(g, seed=17)
+    h = P.lap_setup(g, seed=17, spmv_tpr=kernel)
     x = gg.rhs(g.n, seed=1)
     y = dev(np.zeros(g.n))
     P.lap_laplacian_apply(h, dev(x), y)

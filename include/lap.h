@@ -278,6 +278,39 @@ lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, const int32_t
                                  const double *const *d_B, double *const *d_X, void *stream,
                                  lap_solve_info *infos);
 
+/*
+ * Residual of a graph Laplacian system without any device allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory at all: code running while a CUDA graph
+ * is being captured (where cudaMalloc is not allowed), code inside a process
+ * whose device-memory quota is already spent, or code that must not touch an
+ * allocator shared with other work.  It needs no handle and no allocator:
+ *
+ *   d_r[i] = (b_i - mean(b)) - sum_j w_ij (x_i - x_j)     (r = Pi b - L x)
+ *   h_norms[0] = ||r||_2,  h_norms[1] = ||Pi b||_2        (written on the host)
+ *
+ * for the graph (n, d_row_ptr[n+1] int64, d_col_idx[nnz] int32, d_w[nnz]) in
+ * DEVICE memory, symmetric CSR as everywhere in this library (not checked:
+ * out-of-range indices are the caller's error).  d_x, d_b, d_r are device
+ * n-vectors; d_r may not alias d_x or d_b.  The call synchronises `stream`.
+ *
+ * Scratch: a fixed 1 MiB __device__ array inside this library (every GPU that
+ * loads the library holds it until the process exits) keeps one partial sum
+ * per 256-row tile, so n may be at most 16,777,216; larger n returns
+ * LAP_ERR_UNSUPPORTED before any work is queued.  The first call on a device
+ * looks the array's device address up (cudaGetSymbolAddress) and caches it:
+ * make that first call before any stream capture.  All calls on a device
+ * share the one array, so calls that overlap on the GPU (different streams,
+ * threads or processes sharing a context) race and must be serialised by the
+ * caller.  Allocates nothing: no cudaMalloc, no cudaFree, no library
+ * allocator.
+ */
+lap_status lap_laplacian_residual_noalloc(int64_t n, const int64_t *d_row_ptr,
+                                          const int32_t *d_col_idx, const double *d_w,
+                                          const double *d_x, const double *d_b, double *d_r,
+                                          double *h_norms, void *stream);
+
 /* --- serving: continuous batching of solve requests --- */
 
 typedef struct lap_server_s *lap_server;

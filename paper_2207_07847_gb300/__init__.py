@@ -99,6 +99,8 @@ SIGNATURES = [
     ("lap_get_history", _I32, [_VP, _VP, _I32, C.POINTER(_I32)]),
     ("lap_pcg_solve_host", _I32, [_VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_pcg_solve_batched", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
+    ("lap_laplacian_residual_noalloc", _I32, [_I64, _VP, _VP, _VP, _VP, _VP, _VP,
+                                               C.POINTER(_D), _VP]),
     ("lap_server_options_default", None, [C.POINTER(lap_server_options)]),
     ("lap_server_create", _I32, [C.POINTER(lap_server_options), C.POINTER(_VP)]),
     ("lap_serve_submit", _I32, [_VP, _VP, _I32, _VP, _VP, LAP_DONE_CB, _VP, C.POINTER(_U64)]),
@@ -341,6 +343,16 @@ def lap_pcg_solve_batched(handles, Bs, Xs, stream=None):
     infos = (lap_solve_info * tot)()
     st = lib().lap_pcg_solve_batched(ng, hs, nr, pb, px, _stream(stream), infos)
     return st, list(infos)
+
+
+def lap_laplacian_residual_noalloc(row_ptr, col_idx, w, x, b, r, stream=None):
+    """r = Pi b - L x on device CSR / vectors with no device allocation;
+    returns (status, ||r||, ||Pi b||).  See include/lap.h."""
+    norms = (C.c_double * 2)()
+    n = int(row_ptr.shape[0]) - 1
+    st = lib().lap_laplacian_residual_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(w), _ptr(x),
+                                              _ptr(b), _ptr(r), norms, _stream(stream))
+    return st, norms[0], norms[1]
 
 
 # ---------------------------------------------------------------------------

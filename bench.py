@@ -34,7 +34,7 @@ METRIC = "PCG solves/s at relres 1e-8 and HBM GB/s vs peak; p50/p99 latency vs p
 WORKLOAD = {
     "name": "grid3d_128^3_loguniform[1e-3,1e3]_PEGP_mu0.8",
     "nx": 128, "wlo": 1e-3, "whi": 1e3, "wseed": 3, "prec": "pegp_inner", "mu": 0.8,
-    "tol": 1e-8, "inner_tol": 1e-1, "setup_seed": 1,
+    "tol": 1e-8, "inner_tol": 1e-1, "inner_maxit": 12, "setup_seed": 1,
 }
 CPU_SAMPLE_NX = {"pegp_inner": 16, "msp": 24, "none": 24}   # oracle sample sides
 
@@ -42,8 +42,13 @@ CPU_SAMPLE_NX = {"pegp_inner": 16, "msp": 24, "none": 24}   # oracle sample side
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--aux-steps", type=int, default=1,
+                    help="timed solves of the FP64 comparison, e2e and MSP lines")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="profiling run: one solve of each kind capped at this many outer "
+                         "iterations, nothing timed or printed")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=WORKLOAD["nx"], help="grid side (128 = the workload)")
     ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["pegp_inner", "msp", "none"])
@@ -115,7 +120,8 @@ def oracle_worker(spec_json):
     g = gg.grid3d(spec["nx"], weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
                   seed=WORKLOAD["wseed"])
     M = oracle.make_preconditioner(spec["prec"], g, mu=WORKLOAD["mu"], seed=WORKLOAD["setup_seed"],
-                                   inner_tol=WORKLOAD["inner_tol"], inner_maxit=200)
+                                   inner_tol=WORKLOAD["inner_tol"],
+                                   inner_maxit=WORKLOAD["inner_maxit"])
     from oracle.solve import _laplacian_of
     L = M.ops.L if M.ops is not None else _laplacian_of(g)
     times, work = [], []
@@ -178,21 +184,35 @@ def bench_ours(args, rank, world):
     t0 = time.perf_counter()
     h = P.lap_setup(g, prec=args.prec, mu=WORKLOAD["mu"], precision="mixed",
                     seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"],
-                    inner_tol=WORKLOAD["inner_tol"], maxit=30000)
+                    inner_tol=WORKLOAD["inner_tol"], inner_maxit=WORKLOAD["inner_maxit"],
+                    maxit=30000)
     setup_s = time.perf_counter() - t0
+    if args.profile:
+        # profiling: the kernel mix of each solve kind, few iterations, nothing timed
+        b0 = torch.as_tensor(gg.rhs(g.n, seed=100), device=dev)
+        x0 = torch.empty_like(b0)
+        for precision in ("mixed", "fp64"):
+            P.lap_update_options(h, precision=precision, maxit=args.profile)
+            P.lap_pcg_solve(h, b0, x0)
+        torch.cuda.synchronize()
+        h.close()
+        return None
     info_h = P.lap_get_hierarchy_info(h)
     K, W = args.steps, args.warmup
-    rhs = [gg.rhs(g.n, seed=100 + i + 1000 * rank) for i in range(K + W)]
+    rhs = [gg.rhs(g.n, seed=100 + i + 1000 * rank) for i in range(K + W + max(args.aux_steps, 1))]
     dB = [torch.as_tensor(b, device=dev) for b in rhs]
     hB = [torch.as_tensor(b).pin_memory() for b in rhs]
     x = torch.empty(g.n, dtype=torch.float64, device=dev)
     xh = torch.empty(g.n, dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream()
 
-    def timed(precision, host=False):
-        P.lap_update_options(h, precision=precision)
-        for i in range(W):
-            inf = (P.lap_pcg_solve_host(h, hB[i], xh) if host else P.lap_pcg_solve(h, dB[i], x))
+    def timed(precision, host=False, hh=None, k_steps=None, w_steps=None):
+        hh = hh or h
+        KK = K if k_steps is None else k_steps
+        WW = W if w_steps is None else w_steps
+        P.lap_update_options(hh, precision=precision)
+        for i in range(WW):
+            inf = (P.lap_pcg_solve_host(hh, hB[i], xh) if host else P.lap_pcg_solve(hh, dB[i], x))
             print(f"[bench] warmup {precision} host={host}: {inf.as_dict()}", file=sys.stderr,
                   flush=True)
         if world > 1:
@@ -201,10 +221,10 @@ def bench_ours(args, rank, world):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos, lat = [], []
         ev0.record(stream)
-        for i in range(W, W + K):
+        for i in range(W, W + KK):
             e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e_a.record(stream)
-            inf = (P.lap_pcg_solve_host(h, hB[i], xh) if host else P.lap_pcg_solve(h, dB[i], x))
+            inf = (P.lap_pcg_solve_host(hh, hB[i], xh) if host else P.lap_pcg_solve(hh, dB[i], x))
             e_b.record(stream)
             print(f"[bench] step {precision} host={host}: {inf.as_dict()}", file=sys.stderr,
                   flush=True)
@@ -222,15 +242,16 @@ def bench_ours(args, rank, world):
         lats = sorted(a.elapsed_time(b) for a, b in lat)
         return ms, infos, lats
 
+    def pct(v, q):
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+
+    A = args.aux_steps
     clocks = ClockSampler(dev.index)
     clocks.start()
     ms_mixed, inf_mixed, lat_mixed = timed("mixed")
     clk = clocks.stop()
-    ms_fp64, inf_fp64, lat_fp64 = timed("fp64")
-    ms_e2e, inf_e2e, _ = timed("mixed", host=True)
-
-    def pct(v, q):
-        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+    ms_fp64, inf_fp64, lat_fp64 = timed("fp64", k_steps=A, w_steps=0)
+    ms_e2e, inf_e2e, _ = timed("mixed", host=True, k_steps=A, w_steps=0)
 
     # dominant kernel: the FP32 L_H matvec of the inner solves (PEGP) or the FP32
     # L matvec (MSP / none); timed back to back on the solve's data with CUDA
@@ -250,9 +271,24 @@ def bench_ours(args, rank, world):
         other["spmv_LH_f64"] = {"us": round(m_ * 1e3, 2), "GB/s": round(b_ / (m_ * 1e-3) / 1e9, 1)}
 
     failed = [i.as_dict() for i in inf_mixed + inf_fp64 + inf_e2e if i.status != 0]
+    # the paper's sparsifier alone (MSP) on the same system, for comparison
+    msp = None
+    if args.prec == "pegp_inner":
+        hm = P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="mixed",
+                         seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"], maxit=30000)
+        ms_mm, inf_mm, lat_mm = timed("mixed", hh=hm, k_steps=A, w_steps=1)
+        ms_mf, inf_mf, lat_mf = timed("fp64", hh=hm, k_steps=A, w_steps=0)
+        msp = {"mixed": {"value": A * world / (ms_mm * 1e-3), "unit": "solves/s",
+                         "latency_ms": {"p50": pct(lat_mm, 0.5), "p99": pct(lat_mm, 0.99)},
+                         "iterations": statistics.median(i.iterations for i in inf_mm)},
+               "fp64": {"value": A * world / (ms_mf * 1e-3), "unit": "solves/s",
+                        "latency_ms": {"p50": pct(lat_mf, 0.5), "p99": pct(lat_mf, 0.99)},
+                        "iterations": statistics.median(i.iterations for i in inf_mf)},
+               "failed": [i.as_dict() for i in inf_mm + inf_mf if i.status != 0]}
+        hm.close()
     value = K * world / (ms_mixed * 1e-3)
-    fp64_value = K * world / (ms_fp64 * 1e-3)
-    e2e_value = K * world / (ms_e2e * 1e-3)
+    fp64_value = A * world / (ms_fp64 * 1e-3)
+    e2e_value = A * world / (ms_e2e * 1e-3)
     it_mixed = statistics.median(i.iterations for i in inf_mixed)
     it_fp64 = statistics.median(i.iterations for i in inf_fp64)
     inner_fp64 = statistics.median(i.inner_iterations for i in inf_fp64)
@@ -285,6 +321,7 @@ def bench_ours(args, rank, world):
                      "us_per_launch": round(kms * 1e3, 2), "traffic": None},
         "kernels": other,
         "clocks": clk,
+        "msp_same_system": msp,
         "failed_solves": failed,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -343,7 +380,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
     res = bench_ours(args, rank, world)
-    if rank == 0:
+    if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch

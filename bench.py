@@ -37,6 +37,9 @@ WORKLOAD = {
     "tol": 1e-8, "inner_tol": 1e-1, "inner_maxit": 12, "setup_seed": 1,
 }
 CPU_SAMPLE_NX = {"pegp_inner": 16, "msp": 24, "none": 24}   # oracle sample sides
+# DRAM bytes per launch of the dominant kernel from an ncu capture, scaled to the
+# 128^3 workload (profiles/k_sell_f32_LH_grid3d96.md); None once the kernel changes.
+MEASURED_TRAFFIC = {"spmv_LH": 1.872e9}
 
 
 def parse():
@@ -318,7 +321,8 @@ def bench_ours(args, rank, world):
         "roofline": {"bound": "hbm", "kernel": f"{kern} (FP32)", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_kind": peak_kind, "bytes_per_launch": kbytes,
-                     "us_per_launch": round(kms * 1e3, 2), "traffic": None},
+                     "us_per_launch": round(kms * 1e3, 2),
+                     "traffic": MEASURED_TRAFFIC.get(kern) if args.nx == 128 else None},
         "kernels": other,
         "clocks": clk,
         "msp_same_system": msp,

@@ -269,7 +269,8 @@ lap_status lap_pcg_solve_host(lap_handle h, const double *h_b, double *h_x, void
  * Solve many systems together: graph g in [0, ng) has nrhs[g] right-hand
  * sides stored column after column in d_B[g] (n_g * nrhs[g] doubles, column
  * j at offset j * n_g); solutions go to d_X[g] in the same layout.  All
- * handles must use LAP_PREC_MSP or LAP_PREC_NONE.  Every (graph, column)
+ * handles must use LAP_PREC_MSP (with at least two levels) or LAP_PREC_NONE,
+ * else LAP_ERR_UNSUPPORTED.  Every (graph, column)
  * pair runs its own CG with its own scalars and stops on its own; the
  * matvecs and sweeps of all pairs are batched.  infos (optional) receives
  * sum(nrhs) entries in (graph, column) order.

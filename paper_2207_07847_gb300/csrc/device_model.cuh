@@ -56,6 +56,8 @@ template <typename V> struct DevCsr {
     int *lchunk_ptr = nullptr, *chunk_row = nullptr;
     int64_t *chunk_beg = nullptr;
     V *chunk_part = nullptr;           // per-chunk partial sums (scratch)
+    unsigned char *is_long = nullptr;  // per row: 1 if a long row (batched SpMM)
+    int *lrow_of = nullptr;            // per row: its index among the long rows
     int64_t ell_entries = 0, long_entries = 0;
     int kernel = 0;
 };

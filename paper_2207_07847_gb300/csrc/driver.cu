@@ -1,14 +1,15 @@
 // Device upload, kernel sequencing and the CG drivers of a solver handle.
 //
 // Per CG iteration on L (Section 4 recast on n unknowns, see lap.h):
-//   k_spmv          q = L p, p.q -> alpha
-//   k_update_up1    x += alpha p, r -= alpha q, ||r|| test; level-1 restriction
-//                   and elimination of T's finest aggregates (Section 3.3)
-//   k_msp_up        levels 2 .. l-1: restriction + elimination
-//   k_coarse        top level: dense pseudo-inverse of mu^(2(l-1)) L_l
-//   k_msp_down      levels l-1 .. 2: back-substitution + Horner prolongation
-//   k_msp_down1     z = P(mu) y on level 1, sums for the projection and rho/beta
-//   k_pupdate       p = Pi z + beta p
+//   k_sell            q = L p, p.q -> alpha
+//   k_up_tiled<1>     x += alpha p, r -= alpha q, ||r|| test; level-1 restriction
+//                     and elimination of T's finest aggregates (Section 3.3)
+//   k_up_tiled<0>     middle levels: restriction + elimination
+//   k_msp_tail        the deepest levels up, the top-level pseudo-inverse of
+//                     mu^(2(l-1)) L_l, and back down, in one block
+//   k_down_tiled      middle levels: back-substitution + prolongation
+//   k_down_tiled<1>   z on level 1, sums for the projection and rho/beta
+//   k_pupdate         p = Pi z + beta p
 // captured as a CUDA graph of `check_every` iterations; every kernel returns at
 // once when the device-side convergence flag is set.
 #include <cuda_runtime.h>
@@ -102,8 +103,20 @@ lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, Dev
         d.lchunk_ptr = share->lchunk_ptr;
         d.chunk_row = share->chunk_row;
         d.chunk_beg = share->chunk_beg;
+        d.is_long = share->is_long;
+        d.lrow_of = share->lrow_of;
         d.kernel = share->kernel;
     } else {
+        if (!sl.lrow.empty()) {
+            std::vector<unsigned char> isl(static_cast<size_t>(c.n), 0);
+            std::vector<int32_t> lof(static_cast<size_t>(c.n), -1);
+            for (size_t r = 0; r < sl.lrow.size(); ++r) {
+                isl[sl.lrow[r]] = 1;
+                lof[sl.lrow[r]] = static_cast<int32_t>(r);
+            }
+            LAP_TRY(upload(h, &d.is_long, isl));
+            LAP_TRY(upload(h, &d.lrow_of, lof));
+        }
         LAP_TRY(upload(h, &d.lchunk_ptr, sl.lchunk_ptr));
         LAP_TRY(upload(h, &d.chunk_row, sl.chunk_row));
         LAP_TRY(upload(h, &d.chunk_beg, sl.chunk_beg));
@@ -227,13 +240,6 @@ lap_status alloc_state(lap_handle_s &h, CgState &st)
     return LAP_OK;
 }
 
-int auto_tpr(double avg)
-{
-    int t = 1;
-    while (t < 32 && t < avg) t <<= 1;
-    return t;
-}
-
 // Matvec autotuner: time SELL-32 and CSR with 2..16 threads per row on the
 // matrix itself (FP64, 5 launches each after a warm-up) and keep the fastest.
 template <typename V, int MODE>
@@ -320,10 +326,8 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
     h.launches += plain ? 1 : (M.levels == 1 ? 2 : 2 * ((M.tail0 >= 1 ? M.tail0 : M.levels - 1) - 1) + 3);
     if (plain || M.levels == 1) {
         const int g = grid_for(h, n);
-#define LAP_UPD(U, P)                                                                             \
-    k_update_up1<V, U, false, P><<<g, kBlock, 0, s>>>(n, 0, nullptr, nullptr, nullptr, w.x, w.r,  \
-                                                       w.p, w.q, nullptr, nullptr, V(0), sc,      \
-                                                       st.part, st.ticket)
+#define LAP_UPD(U, P) \
+    k_update<V, U, P><<<g, kBlock, 0, s>>>(n, w.x, w.r, w.p, w.q, nullptr, sc, st.part, st.ticket)
         if (update && plain) LAP_UPD(true, true);
         else if (update) LAP_UPD(true, false);
         else if (plain) LAP_UPD(false, true);
@@ -337,20 +341,21 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
     const int l = M.levels;
     const auto &L0 = M.lev[0];
     if (update)
-        k_update_up1<V, true, true, false><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(
-            n, L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
-            sc, st.part, st.ticket);
+        k_up_tiled<V, 1><<<grid_for(h, L0.nagg), kTA, 0, s>>>(
+            L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
+            nullptr, sc, st.part, st.ticket);
     else
-        k_update_up1<V, false, true, false><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(
-            n, L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
-            sc, st.part, st.ticket);
+        k_up_tiled<V, 2><<<grid_for(h, L0.nagg), kTA, 0, s>>>(
+            L0.nagg, L0.seg, L0.inv, L0.lcf, w.x, w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0],
+            nullptr, sc, st.part, st.ticket);
     // levels below the fused tail one launch each, the tail in one block
     const int t0 = M.tail0 >= 1 ? M.tail0 : l - 1;
     for (int k = 1; k < t0; ++k) {
         const auto &Lk = M.lev[k];
-        k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
-                                                           w.A + M.off[k], w.A + M.off[k + 1],
-                                                           M.gamma[k], nullptr, sc);
+        V *a = w.A + M.off[k];
+        k_up_tiled<V, 0><<<grid_for(h, Lk.nagg), kTA, 0, s>>>(
+            Lk.nagg, Lk.seg, Lk.inv, Lk.lcf, nullptr, a, nullptr, nullptr, a, w.A + M.off[k + 1],
+            M.gamma[k], nullptr, sc, nullptr, nullptr);
     }
     if (M.tail0 >= 1) {
         TailParams<V> P = M.tail_n;
@@ -365,13 +370,13 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
     }
     for (int k = t0 - 1; k >= 1; --k) {
         const auto &Lk = M.lev[k];
-        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, w.A + M.off[k],
-                                                             w.Y + M.off[k + 1], w.Y + M.off[k], V(1),
-                                                             static_cast<V>(M.c[k]), sc);
+        k_down_tiled<V, false><<<grid_for(h, Lk.nagg), kTA, 0, s>>>(
+            Lk.n, Lk.nagg, Lk.seg, w.A + M.off[k], w.Y + M.off[k + 1], w.Y + M.off[k], V(1),
+            static_cast<V>(M.c[k]), nullptr, nullptr, sc, nullptr, nullptr);
     }
-    k_msp_down1<V><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(n, L0.nagg, L0.seg, w.A, w.Y + M.off[1],
-                                                          w.r, w.q, w.z, V(1), V(1), sc, st.part,
-                                                          st.ticket);
+    k_down_tiled<V, true><<<grid_for(h, L0.nagg), kTA, 0, s>>>(n, L0.nagg, L0.seg, w.A, w.Y + M.off[1],
+                                                              w.z, V(1), V(1), w.r, w.q, sc, st.part,
+                                                              st.ticket);
 }
 
 template <typename V>
@@ -394,9 +399,10 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
     h.launches += 2 * up_end + 1;
     for (int k = 0; k < up_end; ++k) {
         const auto &Lk = M.lev[k];
-        k_msp_up<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, Lk.inv, Lk.lcf,
-                                                           A + M.off[k], A + M.off[k + 1], V(1),
-                                                           A + M.off[k + 1], sc);
+        V *a = A + M.off[k];
+        k_up_tiled<V, 0><<<grid_for(h, Lk.nagg), kTA, 0, s>>>(
+            Lk.nagg, Lk.seg, Lk.inv, Lk.lcf, nullptr, a, nullptr, nullptr, a, A + M.off[k + 1], V(1),
+            A + M.off[k + 1], const_cast<CgScalars *>(sc), nullptr, nullptr);
     }
     if (M.tail0 >= 1) {
         TailParams<V> P = M.tail_t;
@@ -411,9 +417,9 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
     }
     for (int k = up_end - 1; k >= 0; --k) {
         const auto &Lk = M.lev[k];
-        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, A + M.off[k],
-                                                             Y + M.off[k + 1], Y + M.off[k], V(1), V(1),
-                                                             sc);
+        k_down_tiled<V, false><<<grid_for(h, Lk.nagg), kTA, 0, s>>>(
+            Lk.n, Lk.nagg, Lk.seg, A + M.off[k], Y + M.off[k + 1], Y + M.off[k], V(1), V(1), nullptr,
+            nullptr, const_cast<CgScalars *>(sc), nullptr, nullptr);
     }
 }
 
@@ -439,7 +445,8 @@ void restrict_tilde(const lap_handle_s &h, const DevMsp<V> &M, const V *r, V *rt
 }
 
 // t = P(mu) y~ by Horner from the top (tree order): T holds t_k on levels >= 2;
-// the finest level goes through k_msp_down1 with the outer CG's reductions.
+// the finest level goes through the finest down pass with the outer CG's
+// reductions.
 template <typename V>
 void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, V *T,
                         const CgVectors<V> &w, const CgState &st, cudaStream_t s)
@@ -450,14 +457,14 @@ void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, 
     k_copy2<V><<<grid_for(h, M.ntop), kBlock, 0, s>>>(M.ntop, yt + ot, T + ot, nullptr, st.sc);
     for (int k = l - 2; k >= 1; --k) {
         const auto &Lk = M.lev[k];
-        k_msp_down<V><<<grid_for(h, Lk.nagg), kBlock, 0, s>>>(Lk.nagg, Lk.seg, yt + M.off[k],
-                                                             T + M.off[k + 1], T + M.off[k], -M.mu, V(1),
-                                                             st.sc);
+        k_down_tiled<V, false><<<grid_for(h, Lk.nagg), kTA, 0, s>>>(
+            Lk.n, Lk.nagg, Lk.seg, yt + M.off[k], T + M.off[k + 1], T + M.off[k], -M.mu, V(1), nullptr,
+            nullptr, st.sc, nullptr, nullptr);
     }
     const auto &L0 = M.lev[0];
-    k_msp_down1<V><<<grid_for(h, L0.nagg), kBlock, 0, s>>>(static_cast<int>(M.off[1]), L0.nagg, L0.seg,
-                                                          yt, T + M.off[1], w.r, w.q, w.z, -M.mu, V(1),
-                                                          st.sc, st.part, st.ticket);
+    k_down_tiled<V, true><<<grid_for(h, L0.nagg), kTA, 0, s>>>(
+        static_cast<int>(M.off[1]), L0.nagg, L0.seg, yt, T + M.off[1], w.z, -M.mu, V(1), w.r, w.q,
+        st.sc, st.part, st.ticket);
 }
 
 // One expanded-space CG iteration of the PEGP inner solve L_H y~ = r~ with the
@@ -469,9 +476,8 @@ void inner_iteration(const lap_handle_s &h, const DevCsr<V> &H, const DevMsp<V> 
     const int64_t nt = M.off[M.levels];
     spmv<V, 0>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
     h.launches += 2;
-    k_update_up1<V, true, false, false><<<grid_for(h, nt), kBlock, 0, s>>>(
-        static_cast<int>(nt), 0, nullptr, nullptr, nullptr, e.x, e.r, e.p, e.q, e.A, nullptr, V(0),
-        st.sc, st.part, st.ticket);
+    k_update<V, true, false><<<grid_for(h, nt), kBlock, 0, s>>>(static_cast<int>(nt), e.x, e.r, e.p,
+                                                                e.q, e.A, st.sc, st.part, st.ticket);
     msp_tilde<V>(h, M, e.A, e.Y, st.sc, s);
     k_zred<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.Y, e.r, st.sc, st.part, st.ticket);
     pupdate<V>(h, nt, e.Y, e.p, st, s);
@@ -591,9 +597,9 @@ lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int
     }
     if (update) {
         h.launches += 1;
-        k_update_up1<V, true, false, false><<<grid_for(h, n), kBlock, 0, s>>>(
-            static_cast<int>(n), 0, nullptr, nullptr, nullptr, w.x, w.r, w.p, w.q, nullptr, nullptr,
-            V(0), st.sc, st.part, st.ticket);
+        k_update<V, true, false><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), w.x, w.r, w.p,
+                                                                   w.q, nullptr, st.sc, st.part,
+                                                                   st.ticket);
     }
     CgScalars sc;
     LAP_TRY(poll(h, st, sc));
@@ -924,6 +930,7 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
 void destroy_handle(lap_handle_s &h)
 {
     if (h.s) cudaStreamSynchronize(h.s);
+    h.batch.reset();
     for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32})
         if (*g) {
             cudaGraphExecDestroy(*g);
@@ -1021,9 +1028,9 @@ lap_status block_prolong(lap_handle_s &h, const double *yt, double *z, cudaStrea
                                                             nullptr);
     for (int k = l - 2; k >= 0; --k) {
         const auto &Lk = M.lev[k];
-        k_msp_down<double><<<grid_for(h, Lk.nagg), kBlock, 0, h.s>>>(
-            Lk.nagg, Lk.seg, h.w64.Y + M.off[k], h.w64.T + M.off[k + 1], h.w64.T + M.off[k], -M.mu, 1.0,
-            nullptr);
+        k_down_tiled<double, false><<<grid_for(h, Lk.nagg), kTA, 0, h.s>>>(
+            Lk.n, Lk.nagg, Lk.seg, h.w64.Y + M.off[k], h.w64.T + M.off[k + 1], h.w64.T + M.off[k],
+            -M.mu, 1.0, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
     k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, h.s>>>(n, h.perm1, h.w64.T, z, nullptr);
     return leave(h, user);
@@ -1142,10 +1149,9 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
                                nullptr, h.stb, s); break;
             case 2: precond_msp<V>(h, M, w, h.stb, false, false, s); break;
             default:
-                k_update_up1<V, true, true, false><<<grid_for(h, M.lev[0].nagg), kBlock, 0, s>>>(
-                    static_cast<int>(n), M.lev[0].nagg, M.lev[0].seg, M.lev[0].inv, M.lev[0].lcf, w.x,
-                    w.r, w.p, w.q, w.A, w.A + M.off[1], M.gamma[0], h.stb.sc, h.stb.part,
-                    h.stb.ticket);
+                k_up_tiled<V, 1><<<grid_for(h, M.lev[0].nagg), kTA, 0, s>>>(
+                    M.lev[0].nagg, M.lev[0].seg, M.lev[0].inv, M.lev[0].lcf, w.x, w.r, w.p, w.q, w.A,
+                    w.A + M.off[1], M.gamma[0], nullptr, h.stb.sc, h.stb.part, h.stb.ticket);
             }
         };
         const double sv = sizeof(V);

@@ -286,82 +286,29 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
 }
 
 // ---------------------------------------------------------------------------
-// Fused CG update + finest-level restriction and elimination (one thread per
-// level-2 aggregate, whose members are contiguous):
-//   UPDATE: x += alpha p, r -= alpha q                  (CG step)
-//   reduce ||r||^2, sum r                               (convergence test)
-//   SWEEP : a_1 = r; delta_1 = M_A^{-1} a_A per aggregate A  (Section 3.3)
-//           a_2(J) = gamma * sum_{u in J} a_1(u)        (restriction)
-// M_A = s L_intra(A) + pw diag(out): leftovers are eliminated onto the pair
-// (coefficients g_a, g_b, 1/d), the pair is solved with the inverse 2x2 Schur
-// complement, leftovers are back-substituted.  The finalise step tests
-// convergence and advances the iteration counter.
+// CG step without a sweep: x += alpha p, r -= alpha q (UPDATE), reduce ||r||^2
+// and sum r, test convergence; rcopy (if given) receives the updated r.  PLAIN
+// (unpreconditioned CG) also forms rho = r^T Pi r and beta.
 // ---------------------------------------------------------------------------
-// PLAIN (no sweep): unpreconditioned CG, the finalise step also forms
-// rho = r^T Pi r and beta.  Without SWEEP, d1 (if not null) receives a copy of
-// the updated r (input of an in-place sweep that follows).
-template <typename V, bool UPDATE, bool SWEEP, bool PLAIN>
+template <typename V, bool UPDATE, bool PLAIN>
 __global__ void __launch_bounds__(kBlock)
-k_update_up1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
-             const V *__restrict__ lcf, V *__restrict__ x, V *__restrict__ r,
-             const V *__restrict__ p, const V *__restrict__ q, V *__restrict__ d1,
-             V *__restrict__ a2, V gamma, CgScalars *sc, double *part, unsigned *ticket)
+k_update(int n, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
+         const V *__restrict__ q, V *__restrict__ rcopy, CgScalars *sc, double *part,
+         unsigned *ticket)
 {
     if (halted(sc)) return;
     double rr = 0.0, rs = 0.0;
     const V al = UPDATE ? (V)sc->alpha : V(0);
-    if (SWEEP) {
-        for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
-            const int b0 = seg[J], e = seg[J + 1];
-            V ra = r[b0], rb = r[b0 + 1];
-            if (UPDATE) {
-                x[b0] += al * p[b0];
-                x[b0 + 1] += al * p[b0 + 1];
-                ra -= al * q[b0];
-                rb -= al * q[b0 + 1];
-                r[b0] = ra;
-                r[b0 + 1] = rb;
-            }
-            rr += (double)ra * ra + (double)rb * rb;
-            rs += (double)ra + (double)rb;
-            V sum = ra + rb, ha = ra, hb = rb;
-            const V *lc = lcf + 3 * (b0 - 2 * J);
-            for (int t = b0 + 2; t < e; ++t) {
-                V rl = r[t];
-                if (UPDATE) {
-                    x[t] += al * p[t];
-                    rl -= al * q[t];
-                    r[t] = rl;
-                }
-                rr += (double)rl * rl;
-                rs += (double)rl;
-                sum += rl;
-                const V *c = lc + 3 * (t - b0 - 2);
-                ha += c[0] * rl;
-                hb += c[1] * rl;
-            }
-            V da, db;
-            pair_solve(inv + 4 * J, ha, hb, da, db);
-            d1[b0] = da;
-            d1[b0 + 1] = db;
-            for (int t = b0 + 2; t < e; ++t) {
-                const V *c = lc + 3 * (t - b0 - 2);
-                d1[t] = r[t] * c[2] + c[0] * da + c[1] * db;
-            }
-            a2[J] = gamma * sum;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        V ri = r[i];
+        if (UPDATE) {
+            x[i] += al * p[i];
+            ri -= al * q[i];
+            r[i] = ri;
         }
-    } else {
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-            V ri = r[i];
-            if (UPDATE) {
-                x[i] += al * p[i];
-                ri -= al * q[i];
-                r[i] = ri;
-            }
-            if (d1) d1[i] = ri;
-            rr += (double)ri * ri;
-            rs += (double)ri;
-        }
+        if (rcopy) rcopy[i] = ri;
+        rr += (double)ri * ri;
+        rs += (double)ri;
     }
     double v[2] = {rr, rs};
     if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
@@ -376,7 +323,7 @@ k_update_up1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__
             else if (rel <= sc->tol) sc->flag = kConverged;
             else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
         }
-        if (!SWEEP && PLAIN) {
+        if (PLAIN) {
             // unpreconditioned CG: z = Pi r
             const double m = v[1] / (double)n;
             const double rho_new = v[0] - m * v[1];
@@ -385,41 +332,6 @@ k_update_up1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__
             sc->rho = rho_new;
             sc->first = 0;
         }
-    }
-}
-
-// Restriction + elimination on level k >= 2 (thread per level-(k+1) aggregate).
-// a holds a_k on entry and delta_k on exit; anext(J) = gamma*sum a_k + f_{k+1}(J).
-template <typename V>
-__global__ void __launch_bounds__(kBlock)
-k_msp_up(int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
-         const V *__restrict__ lcf, V *__restrict__ a, V *anext, V gamma,
-         const V *fnext, const CgScalars *sc)
-{
-    if (halted(sc)) return;
-    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
-        const int b0 = seg[J], e = seg[J + 1];
-        const V aa = a[b0], ab = a[b0 + 1];
-        V sum = aa + ab, ha = aa, hb = ab;
-        const V *lc = lcf + 3 * (b0 - 2 * J);
-        for (int t = b0 + 2; t < e; ++t) {
-            const V al = a[t];
-            const V *c = lc + 3 * (t - b0 - 2);
-            sum += al;
-            ha += c[0] * al;
-            hb += c[1] * al;
-        }
-        V da, db;
-        pair_solve(inv + 4 * J, ha, hb, da, db);
-        for (int t = b0 + 2; t < e; ++t) {
-            const V *c = lc + 3 * (t - b0 - 2);
-            a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
-        }
-        a[b0] = da;
-        a[b0 + 1] = db;
-        V nx = gamma * sum;
-        if (fnext) nx += fnext[J];
-        anext[J] = nx;
     }
 }
 
@@ -441,23 +353,189 @@ k_coarse(int m, const double *__restrict__ G, const V *__restrict__ a, V *__rest
     if (lane == 0) y[row] = (V)(scale * s);
 }
 
-// Top-down pass over one level (thread per level-(k+1) aggregate J):
-//     out_k(u) = pc * parent(J) + dc * delta_k(u)      for u in J.
-// (pc, dc) = (1, c_k): MSP prolongation z = sum_k c_k delta_k(anc_k(u)) with
-//   c_k = sum_{i<k} (-mu)^i > 0, i.e. P(mu) applied to the back-substituted
+// ---------------------------------------------------------------------------
+// Shared-memory-staged sweeps.  A block takes kTA consecutive aggregates of a
+// level; in tree order their members are one contiguous range [v0, v1), which
+// the block reads (and updates) with coalesced accesses, stages in shared
+// memory, solves aggregate by aggregate (one thread each) and writes back
+// coalesced.  A tile whose range exceeds kTV members (a hub aggregate) works
+// on global memory directly.
+// ---------------------------------------------------------------------------
+constexpr int kTA = 256;      // aggregates per tile (= threads per block)
+constexpr int kTV = 1536;     // staged members per tile
+
+// Elimination of one aggregate (Section 3.3): a = its members' right-hand
+// sides (pair first, then leftovers), d = their solution (may alias a).
+// Returns the sum of a (the restriction to the parent).
+template <typename V>
+__device__ __forceinline__ V agg_eliminate(const V *a, V *d, int cnt, const V *lc, const V *cf)
+{
+    const V aa = a[0], ab = a[1];
+    V sum = aa + ab, ha = aa, hb = ab;
+    for (int t = 2; t < cnt; ++t) {
+        const V al = a[t];
+        const V *c = lc + 3 * (t - 2);
+        sum += al;
+        ha += c[0] * al;
+        hb += c[1] * al;
+    }
+    V da, db;
+    pair_solve(cf, ha, hb, da, db);
+    for (int t = 2; t < cnt; ++t) {
+        const V *c = lc + 3 * (t - 2);
+        d[t] = a[t] * c[2] + c[0] * da + c[1] * db;
+    }
+    d[0] = da;
+    d[1] = db;
+    return sum;
+}
+
+// Upward pass over one level, tiled.
+// MODE 0: a (the r argument) holds a_k and is overwritten by delta_k (dout == r)
+// MODE 1: finest level with the CG step: x += alpha p, r -= alpha q, then
+//         a_1 = r, delta_1 -> dout; reduces ||r||^2, sum r and finalises the
+//         convergence test
+// MODE 2: finest level without the step (start of a solve), reduces as MODE 1
+// anext(J) = gamma * sum_{u in J} a(u) (+ fnext(J) if given; may alias anext).
+template <typename V, int MODE>
+__global__ void __launch_bounds__(kTA)
+k_up_tiled(int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
+           const V *__restrict__ lcf, V *__restrict__ x, V *r, const V *__restrict__ p,
+           const V *__restrict__ q, V *dout, V *anext, V gamma, const V *fnext, CgScalars *sc,
+           double *part, unsigned *ticket)
+{
+    if (halted(sc)) return;
+    __shared__ V sa[kTV];
+    __shared__ int sseg[kTA + 1];
+    const int tid = threadIdx.x;
+    const V al = MODE == 1 ? (V)sc->alpha : V(0);
+    double rr = 0.0, rs = 0.0;
+    const int ntiles = (nagg + kTA - 1) / kTA;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int J0 = tile * kTA;
+        const int na = min(kTA, nagg - J0);
+        for (int i = tid; i <= na; i += kTA) sseg[i] = seg[J0 + i];
+        __syncthreads();
+        const int v0 = sseg[0], nv = sseg[na] - v0;
+        const bool staged = nv <= kTV;
+        for (int i = tid; i < nv; i += kTA) {
+            V ri;
+            if (MODE == 1) {
+                x[v0 + i] += al * p[v0 + i];
+                ri = r[v0 + i] - al * q[v0 + i];
+                r[v0 + i] = ri;
+            } else {
+                ri = r[v0 + i];
+            }
+            if (MODE != 0) {
+                rr += (double)ri * (double)ri;
+                rs += (double)ri;
+            }
+            if (staged) sa[i] = ri;
+        }
+        __syncthreads();
+        if (tid < na) {
+            const int J = J0 + tid;
+            const int b = sseg[tid] - v0, e = sseg[tid + 1] - v0;
+            const V *src = staged ? sa + b : r + v0 + b;
+            V *dst = staged ? sa + b : dout + v0 + b;
+            const V sum = agg_eliminate(src, dst, e - b, lcf + 3 * (v0 + b - 2 * J), inv + 4 * J);
+            V nx = gamma * sum;
+            if (fnext) nx += fnext[J];
+            anext[J] = nx;
+        }
+        __syncthreads();
+        if (staged)
+            for (int i = tid; i < nv; i += kTA) dout[v0 + i] = sa[i];
+        __syncthreads();
+    }
+    if (MODE == 0) return;
+    double v[2] = {rr, rs};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        sc->rr = v[0];
+        sc->rs = v[1];
+        if (MODE == 1) {
+            sc->iter += 1;
+            const double rel = sqrt(v[0]) / sc->bnorm;
+            sc->relres = rel;
+            if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
+            if (!isfinite(rel)) sc->flag = kBreakdown;
+            else if (rel <= sc->tol) sc->flag = kConverged;
+            else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+        }
+    }
+}
+
+// Downward pass over one level, tiled: out(u) = pc * parent(J) + dc * delta(u).
+// (pc, dc) = (1, c_k): MSP prolongation z = sum_k c_k delta_k(anc_k(u)), with
+//   c_k = sum_{i<k} (-mu)^i > 0: P(mu) applied to the back-substituted
 //   sparsifier solution without the alternating Horner sum (Section 3.3);
 // (1, 1): back-substitution y_k = y_{k+1}(J) + delta_k (expanded-space solve);
 // (-mu, 1): Horner step t_k = y_k - mu t_{k+1}(J) of P(mu) y (Section 2.2).
-template <typename V>
-__global__ void __launch_bounds__(kBlock)
-k_msp_down(int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
-           const V *__restrict__ parent, V *__restrict__ out, V pc, V dc, const CgScalars *sc)
+// FINEST: out is the preconditioned residual z; reduces sum z, r.z, z.q and
+// finalises zmean, rho and beta (standard, or flexible FCG).
+template <typename V, bool FINEST>
+__global__ void __launch_bounds__(kTA)
+k_down_tiled(int n, int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
+             const V *__restrict__ parent, V *__restrict__ out, V pc, V dc, const V *__restrict__ r,
+             const V *__restrict__ q, CgScalars *sc, double *part, unsigned *ticket)
 {
     if (halted(sc)) return;
-    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
-        const int b0 = seg[J], e = seg[J + 1];
-        const V base = pc * parent[J];
-        for (int u = b0; u < e; ++u) out[u] = base + dc * delta[u];
+    __shared__ V sb[kTV];
+    __shared__ int sseg[kTA + 1];
+    const int tid = threadIdx.x;
+    const bool flex = FINEST && sc->flexible && !sc->first;
+    double sz = 0.0, srz = 0.0, szq = 0.0;
+    const int ntiles = (nagg + kTA - 1) / kTA;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int J0 = tile * kTA;
+        const int na = min(kTA, nagg - J0);
+        for (int i = tid; i <= na; i += kTA) sseg[i] = seg[J0 + i];
+        __syncthreads();
+        const int v0 = sseg[0], nv = sseg[na] - v0;
+        const bool staged = nv <= kTV;
+        if (tid < na) {
+            const V base = pc * parent[J0 + tid];
+            for (int u = sseg[tid]; u < sseg[tid + 1]; ++u) {
+                if (staged) {
+                    sb[u - v0] = base;
+                } else {
+                    const V o = base + dc * delta[u];
+                    out[u] = o;
+                    if (FINEST) {
+                        sz += (double)o;
+                        srz += (double)r[u] * (double)o;
+                        if (flex) szq += (double)o * (double)q[u];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (staged) {
+            for (int i = tid; i < nv; i += kTA) {
+                const V o = sb[i] + dc * delta[v0 + i];
+                out[v0 + i] = o;
+                if (FINEST) {
+                    sz += (double)o;
+                    srz += (double)r[v0 + i] * (double)o;
+                    if (flex) szq += (double)o * (double)q[v0 + i];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!FINEST) return;
+    double v[3] = {sz, srz, szq};
+    if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
+        const double m = v[0] / (double)n;
+        const double rho_new = v[1] - m * sc->rs;
+        sc->zmean = m;
+        if (sc->first) sc->beta = 0.0;
+        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
+        else sc->beta = rho_new / sc->rho;
+        sc->rho = rho_new;
+        sc->first = 0;
+        if (!isfinite(rho_new)) sc->flag = kBreakdown;
     }
 }
 
@@ -595,46 +673,8 @@ k_copy2(int64_t n, const V *__restrict__ in, V *__restrict__ o1, V *__restrict__
     }
 }
 
-// Finest level of the top-down pass, producing the preconditioned residual
-// z(u) = pc * parent(J) + dc * delta_1(u) and the reductions for the projection
-// and the CG scalars: sum z, r.z, z.q  ->  zmean, rho and beta (standard or
-// flexible).
-template <typename V>
-__global__ void __launch_bounds__(kBlock)
-k_msp_down1(int n, int nagg, const int *__restrict__ seg, const V *__restrict__ delta,
-            const V *__restrict__ parent, const V *__restrict__ r, const V *__restrict__ q,
-            V *__restrict__ z, V pc, V dc, CgScalars *sc, double *part, unsigned *ticket)
-{
-    if (halted(sc)) return;
-    double sz = 0.0, srz = 0.0, szq = 0.0;
-    const bool flex = sc->flexible && !sc->first;
-    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < nagg; J += gridDim.x * blockDim.x) {
-        const int b0 = seg[J], e = seg[J + 1];
-        const V base = pc * parent[J];
-        for (int u = b0; u < e; ++u) {
-            const V zu = base + dc * delta[u];
-            z[u] = zu;
-            sz += (double)zu;
-            srz += (double)r[u] * (double)zu;
-            if (flex) szq += (double)zu * (double)q[u];
-        }
-    }
-    double v[3] = {sz, srz, szq};
-    if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
-        const double m = v[0] / (double)n;
-        const double rho_new = v[1] - m * sc->rs;
-        sc->zmean = m;
-        if (sc->first) sc->beta = 0.0;
-        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
-        else sc->beta = rho_new / sc->rho;
-        sc->rho = rho_new;
-        sc->first = 0;
-        if (!isfinite(rho_new)) sc->flag = kBreakdown;
-    }
-}
-
 // Single-level hierarchy: z = G r directly (dense pseudo-inverse), with the
-// same reductions as k_msp_down1.  One warp per row.
+// same reductions as the finest tiled down pass.  One warp per row.
 template <typename V>
 __global__ void __launch_bounds__(kBlock)
 k_dense_z(int n, const double *__restrict__ G, const V *__restrict__ r, const V *__restrict__ q,

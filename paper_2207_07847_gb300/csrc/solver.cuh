@@ -9,6 +9,10 @@
 #include "device_model.cuh"
 #include "lap_internal.h"
 
+namespace lap {
+struct BatchWork;   // batched-solve workspace (batched.cu)
+}
+
 struct lap_handle_s {
     lap::HostModel m;
     bool host_only = false;
@@ -47,6 +51,7 @@ struct lap_handle_s {
     double *hist = nullptr;           // device history of the last solve (maxit entries)
     int hist_count = 0;
     int hist_capacity = 0;
+    std::shared_ptr<lap::BatchWork> batch;   // allocated by the first batched solve
 };
 
 namespace lap {

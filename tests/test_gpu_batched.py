@@ -1,0 +1,127 @@
+"""Batched solves (many right-hand sides, several graphs) against single solves
+and the oracle, through the C ABI.
+
+Every column of a batched solve runs the same preconditioned CG as a single
+solve of that column: the tests check per-column convergence (true relative
+residual <= 1e-8), agreement with the single-solve solution to within what
+the two residuals allow, iteration counts close to the single solve's, and
+the oracle's solution for one column.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle.expanded import laplacian
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2207_07847_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build_library()
+    P.lib()
+    P.set_torch_allocator()
+    yield
+    torch.cuda.synchronize()
+
+
+def _cols(n, k, seed):
+    return np.stack([gg.rhs(n, seed=seed + j) for j in range(k)])     # (k, n) = column-major n x k
+
+
+def _check_columns(g, B, X, infos, tol=1e-8):
+    L = laplacian(g.adjacency())
+    for j in range(B.shape[0]):
+        b = B[j] - B[j].mean()
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.all(X[j] == 0.0)
+            continue
+        rel = np.linalg.norm(b - L @ X[j]) / nb
+        assert rel <= tol, (j, rel, infos[j].as_dict())
+        assert infos[j].status == 0 and infos[j].relres <= tol
+        assert abs(infos[j].relres - rel) <= 1e-3 * rel + 1e-15
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["msp", "none"])
+def test_batched_columns_match_single_solves(precision, prec):
+    g = gg.grid3d(18, 17, 16, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    B = _cols(g.n, 7, seed=40)                  # padded to 8 columns inside
+    B[3] = 0.0                                  # a zero column stays zero
+    h = P.lap_setup(g, seed=17, prec=prec, precision=precision, maxit=6000)
+    Bd = torch.as_tensor(B, device="cuda")
+    Xd = torch.empty_like(Bd)
+    st, infos = P.lap_pcg_solve_batched([h], [Bd], [Xd])
+    assert st == 0, [i.as_dict() for i in infos]
+    X = Xd.cpu().numpy()
+    _check_columns(g, B, X, infos)
+    L = laplacian(g.adjacency())
+    for j in (0, 5):
+        x1 = torch.empty_like(Bd[j])
+        single = P.lap_pcg_solve(h, Bd[j], x1)
+        assert single.status == 0
+        bp = B[j] - B[j].mean()
+        assert np.linalg.norm(L @ (X[j] - x1.cpu().numpy())) <= 2e-8 * np.linalg.norm(bp)
+        if precision == "fp64":
+            assert abs(infos[j].iterations - single.iterations) <= max(2, 0.03 * single.iterations)
+
+
+def test_batched_column_matches_oracle():
+    g = gg.grid2d(64, weights="uniform", lo=1.0, hi=2.0, seed=1)
+    B = _cols(g.n, 5, seed=7)
+    h = P.lap_setup(g, seed=17, mu=0.8)
+    Bd = torch.as_tensor(B, device="cuda")
+    Xd = torch.empty_like(Bd)
+    st, infos = P.lap_pcg_solve_batched([h], [Bd], [Xd])
+    assert st == 0
+    ref = oracle.solve(g, B[2], "msp", mu=0.8, seed=17)
+    L = laplacian(g.adjacency())
+    bp = B[2] - B[2].mean()
+    assert abs(infos[2].iterations - ref.iters) <= 2
+    assert np.linalg.norm(L @ (Xd[2].cpu().numpy() - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+
+
+def test_batched_power_law_hubs_and_wide_tiles():
+    """R-MAT with hub rows (long-row chunks) and 37 columns (padded to 64)."""
+    g = gg.rmat(12, 16, seed=5)
+    B = _cols(g.n, 37, seed=90)
+    for precision in ("fp64", "mixed"):
+        h = P.lap_setup(g, seed=3, precision=precision, maxit=4000)
+        Bd = torch.as_tensor(B, device="cuda")
+        Xd = torch.empty_like(Bd)
+        st, infos = P.lap_pcg_solve_batched([h], [Bd], [Xd])
+        assert st == 0, precision
+        _check_columns(g, B, Xd.cpu().numpy(), infos)
+
+
+def test_batched_several_graphs_one_call():
+    graphs = [gg.grid2d(40, 33, weights="uniform", seed=2), gg.chung_lu(3000, seed=4),
+              gg.rgg(2500, seed=6)]
+    nrhs = [1, 5, 16]
+    hs = [P.lap_setup(g, seed=9, maxit=5000) for g in graphs]
+    Bs = [torch.as_tensor(_cols(g.n, k, seed=11 * k), device="cuda") for g, k in zip(graphs, nrhs)]
+    Xs = [torch.empty_like(B) for B in Bs]
+    st, infos = P.lap_pcg_solve_batched(hs, Bs, Xs)
+    assert st == 0 and len(infos) == sum(nrhs)
+    off = 0
+    for g, k, B, X in zip(graphs, nrhs, Bs, Xs):
+        _check_columns(g, B.cpu().numpy(), X.cpu().numpy(), infos[off:off + k])
+        off += k
+
+
+def test_batched_more_than_256_columns():
+    g = gg.grid2d(24, weights="uniform", seed=5)
+    B = _cols(g.n, 300, seed=1)
+    h = P.lap_setup(g, seed=2)
+    Bd = torch.as_tensor(B, device="cuda")
+    Xd = torch.empty_like(Bd)
+    st, infos = P.lap_pcg_solve_batched([h], [Bd], [Xd])
+    assert st == 0 and len(infos) == 300
+    _check_columns(g, B, Xd.cpu().numpy(), infos)

@@ -877,7 +877,7 @@ static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flex
 // scalars for timing runs: running, never converging, unit norms
 static __global__ void k_bench_scalars(CgScalars *sc)
 {
-    sc->tol = 0.0;
+    sc->tol = -1.0;                 // never met, even by a zero residual
     sc->maxit = 0x7fffffff;
     sc->flexible = 0;
     sc->iter = 0;

@@ -312,42 +312,91 @@ lap_status lap_laplacian_residual_noalloc(int64_t n, const int64_t *d_row_ptr,
                                           const double *d_x, const double *d_b, double *d_r,
                                           double *h_norms, void *stream);
 
-/* --- serving: continuous batching of solve requests --- */
+/* --- serving: continuous batching of solve requests ---
+ *
+ * A server answers a stream of solve requests L_h X = B on set-up graphs.  It
+ * extends the batched solve above to requests that arrive at any time (the
+ * paper solves one system at a time; serving is this library's addition).
+ * Every graph with requests in flight has a resident column batch of R
+ * columns (R = the smallest power of two >= max(8, max_slots), at most 256)
+ * on its own CUDA stream; a request occupies nrhs contiguous columns of its
+ * graph's batch.  One worker thread alternates between
+ *   - admission: queued requests take free columns; a graph without a batch
+ *     gets one if the device memory of all batches stays within
+ *     hbm_budget_bytes (the first batch is always admitted);
+ *   - one launch of check_every CG iterations of every batch (the batches of
+ *     different graphs overlap on the device).  New requests join a running
+ *     batch at this boundary: only their columns are started, the other
+ *     columns keep their iterates, directions and scalars;
+ *   - retirement: a request whose columns have all stopped (converged,
+ *     iteration limit, breakdown, cancelled, timed out) gets its solution
+ *     (mean-zero, caller's vertex numbering) written to its d_X, its info
+ *     filled and its callback called; its columns become free at once.
+ * Columns run in FP64 whatever the handle's precision option; tol, maxit and
+ * timeout_s come from the handle's options.  Every column's arithmetic is
+ * independent of the other columns and of the moment it joined, so a
+ * request's result is bitwise the same whether it ran alone or with others
+ * on the same server (same handle, same max_slots).
+ *
+ * Threading: the calls below are thread-safe.  While a server holds requests
+ * of a handle, that handle may not be used by any other call (its launch
+ * counter and CUDA graphs belong to the worker), and lap_destroy(h) may be
+ * called only once they have all finished.
+ */
 
 typedef struct lap_server_s *lap_server;
 
 typedef struct lap_server_options {
-    int64_t hbm_budget_bytes;  /* admission budget for request working memory      */
-    int32_t max_slots;         /* maximum (graph, rhs) pairs in flight             */
-    int32_t check_every;       /* iterations between admission/retirement points   */
+    int64_t hbm_budget_bytes;  /* device memory all resident batches may hold (bytes) */
+    int32_t max_slots;         /* columns per graph batch (1..256, rounded up, >= 8) */
+    int32_t check_every;       /* CG iterations between admission / retirement
+                                * points (<= 0: the handle's check_every)          */
     int32_t reserved[8];
 } lap_server_options;
 
-/* Called on the server thread when a request finishes (x already written). */
+/* Called on the server's worker thread when a request finishes, after its
+ * solution has been written (d_X is complete when the callback runs). */
 typedef void (*lap_done_cb)(void *user, uint64_t req_id, const lap_solve_info *info);
 
+/* Defaults: 32 GiB budget, 16 slots, check_every 8. */
 void lap_server_options_default(lap_server_options *opts);
 
-/* Start a server with its own CUDA stream and worker thread on the current device. */
+/* Start a server (worker thread) on the current device.  LAP_ERR_INVALID_ARG
+ * for max_slots outside 1..256 or a budget <= 0. */
 lap_status lap_server_create(const lap_server_options *opts, lap_server *out);
 
 /*
- * Queue a request: solve L_h X = B for nrhs columns (column-major, as in
- * lap_pcg_solve_batched; device pointers that stay valid until completion).
- * Returns immediately with *req_id.  The request joins the running batch as
- * soon as slots and memory allow.  h must use LAP_PREC_MSP or LAP_PREC_NONE.
+ * Queue a request: solve L_h X = B for nrhs columns (column-major as in
+ * lap_pcg_solve_batched: d_B and d_X hold n * nrhs doubles, column j at
+ * offset j * n; device pointers that must stay valid, and d_B unchanged,
+ * until the request has finished).  Returns at once with *req_id (ids start
+ * at 1).  cb (optional) is called on completion.  Errors, returned before
+ * anything is queued: LAP_ERR_INVALID_ARG (null pointer, host-only handle,
+ * nrhs < 1 or nrhs > the batch width R), LAP_ERR_UNSUPPORTED (a
+ * preconditioner other than LAP_PREC_MSP with >= 2 levels or LAP_PREC_NONE),
+ * LAP_ERR_BUSY (one batch of this graph alone exceeds hbm_budget_bytes),
+ * LAP_ERR_CANCELLED (the server is shutting down).
  */
 lap_status lap_serve_submit(lap_server s, lap_handle h, int32_t nrhs, const double *d_B,
                             double *d_X, lap_done_cb cb, void *user, uint64_t *req_id);
 
-/* Block until request req_id is finished or timeout_s elapses (<= 0: forever).
- * Writes its info.  Returns LAP_ERR_TIMEOUT if still running. */
+/*
+ * Block until request req_id has finished or timeout_s seconds have passed
+ * (timeout_s <= 0: no limit).  On completion writes its info (seconds = time
+ * from submission to completion, kernel_launches = kernels of its batch
+ * while it was resident), forgets the id and returns the request's status;
+ * otherwise returns LAP_ERR_TIMEOUT and the request goes on.  An unknown (or
+ * already waited-for) id gives LAP_ERR_INVALID_ARG.
+ */
 lap_status lap_serve_wait(lap_server s, uint64_t req_id, double timeout_s, lap_solve_info *info);
 
-/* Cancel a queued or running request (its info gets LAP_ERR_CANCELLED). */
+/* Cancel a queued or running request: it finishes at the next retirement
+ * point with status LAP_ERR_CANCELLED (a running one with its current iterate
+ * written to d_X).  No effect on a finished request. */
 lap_status lap_serve_cancel(lap_server s, uint64_t req_id);
 
-/* Finish all admitted work, stop the worker and free the server. */
+/* Cancel the queued requests, finish the admitted ones (callbacks run), stop
+ * the worker and free the server and its batches. */
 void lap_server_destroy(lap_server s);
 
 #ifdef __cplusplus

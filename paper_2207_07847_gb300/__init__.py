@@ -12,7 +12,6 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -387,6 +386,65 @@ def clear_allocator():
     _torch_alloc_refs = None
 
 
-@dataclass
-class ServerRef:
-    ptr: int
+def lap_server_options_default() -> lap_server_options:
+    o = lap_server_options()
+    lib().lap_server_options_default(C.byref(o))
+    return o
+
+
+class Server:
+    """A continuous-batching solve server (lap_server_*).
+
+    ``submit(h, B, X)`` queues L_h X = B for a (nrhs, n) float64 CUDA tensor B
+    (one right-hand side per row, i.e. the column-major layout of the C ABI)
+    and returns the request id; ``wait(id)`` blocks until it finished and
+    returns ``(status, info)``.  The tensors and the optional callback are kept
+    alive here until the request has been waited for or the server closed.
+    """
+
+    def __init__(self, hbm_budget_bytes=None, max_slots=None, check_every=None):
+        o = lap_server_options_default()
+        if hbm_budget_bytes is not None:
+            o.hbm_budget_bytes = int(hbm_budget_bytes)
+        if max_slots is not None:
+            o.max_slots = int(max_slots)
+        if check_every is not None:
+            o.check_every = int(check_every)
+        self.options = o
+        p = C.c_void_p()
+        _check(lib().lap_server_create(C.byref(o), C.byref(p)), "lap_server_create")
+        self.ptr = p.value
+        self._keep = {}
+
+    def submit(self, h: Handle, B, X, callback=None) -> int:
+        nrhs = int(B.shape[0]) if B.dim() == 2 else 1
+        cb = LAP_DONE_CB(lambda user, rid, info: callback(int(rid), info.contents.as_dict())) \
+            if callback is not None else LAP_DONE_CB()
+        rid = C.c_uint64(0)
+        st = lib().lap_serve_submit(self.ptr, h.ptr, nrhs, _ptr(B), _ptr(X), cb, None, C.byref(rid))
+        _check(st, "lap_serve_submit")
+        self._keep[rid.value] = (B, X, cb)
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 0.0):
+        info = lap_solve_info()
+        info.status = -1                  # stays -1 while the request runs
+        st = lib().lap_serve_wait(self.ptr, rid, float(timeout_s), C.byref(info))
+        if info.status != -1 or st == 1:  # finished (or unknown id)
+            self._keep.pop(rid, None)
+        return st, info
+
+    def cancel(self, rid: int) -> int:
+        return lib().lap_serve_cancel(self.ptr, rid)
+
+    def close(self):
+        if self.ptr:
+            lib().lap_server_destroy(self.ptr)
+            self.ptr = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,6 +17,8 @@ namespace lap {
 struct BCol {
     double rho, alpha, beta, zmean, pq, qs, rr, rs, bnorm, relres, tol, bmean;
     int iter, flag, first, maxit;
+    int join;          // 1 while a newly admitted column waits for its first direction
+    int pad;
 };
 
 constexpr int kBThreads = 256;
@@ -144,7 +146,7 @@ kb_center(int n, int R, int CT, int nrhs, int subtract, double *__restrict__ src
 }
 
 // Refinement bookkeeping: a running column whose true residual meets tol stops.
-__global__ void kb_refine_flags(int R, int nrhs, BCol *col, double tol)
+static __global__ void kb_refine_flags(int R, int nrhs, BCol *col, double tol)
 {
     for (int c = threadIdx.x; c < R; c += blockDim.x) {
         BCol &C = col[c];
@@ -197,7 +199,7 @@ kb_spmm(int n, int R, int CT, const int *__restrict__ rp, const int *__restrict_
         const int *__restrict__ lrow_of, const int *__restrict__ lchunk_ptr,
         const V *__restrict__ chunk_part, const V *__restrict__ x, V *__restrict__ y,
         const double *__restrict__ Bs, double *__restrict__ yres, BCol *col, double *part,
-        unsigned *ticket)
+        unsigned *ticket, double *tres)
 {
     __shared__ double tot[512];
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
@@ -217,9 +219,9 @@ kb_spmm(int n, int R, int CT, const int *__restrict__ rp, const int *__restrict_
             } else {
                 for (int p = b; p < e; ++p) s += w[p] * (xi - x[(size_t)ci[p] * R + c]);
             }
-            if (MODE == 1) {
+            if (MODE == 1 || MODE == 3) {
                 const double rv = Bs[k] - (double)s;
-                yres[k] = rv;
+                if (MODE == 1) yres[k] = rv;
                 acc[0][j] += rv * rv;
                 acc[1][j] += rv;
             } else {
@@ -235,7 +237,9 @@ kb_spmm(int n, int R, int CT, const int *__restrict__ rp, const int *__restrict_
     if (bcol_reduce<2, 8>(acc, R, CT, part, ticket, tot)) {
         for (int c = threadIdx.x; c < R; c += kBThreads) {
             BCol &C = col[c];
-            if (MODE == 0) {
+            if (MODE == 3) {                 // true residuals only, state untouched
+                tres[c] = C.bnorm > 0.0 ? sqrt(tot[c]) / C.bnorm : 0.0;
+            } else if (MODE == 0) {
                 if (C.flag != kRun) continue;
                 C.pq = tot[c];
                 C.qs = tot[R + c];
@@ -497,6 +501,117 @@ kb_scatter(int n, int R, int CT, int nrhs, const int *__restrict__ perm, const V
         for (int jj = 0; jj < R / CT; ++jj) {
             const int c = cl + jj * CT;
             if (c < nrhs) X[(size_t)c * n + dst] = (double)x[(size_t)i * R + c] - means[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Continuous batching: columns [c0, c0 + k) of a running batch start a new
+// request while the other columns keep iterating.
+// ---------------------------------------------------------------------------
+// Bs(:, c0..c0+k) = the request's columns in tree order; their sums -> bmean.
+static __global__ void __launch_bounds__(kBThreads)
+kb_join_gather(int n, int R, int CT, int c0, int k, const int *__restrict__ perm,
+               const double *__restrict__ B, double *__restrict__ Bs, BCol *col, double *part,
+               unsigned *ticket)
+{
+    __shared__ double tot[256];
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    double acc[1][8];
+    for (int j = 0; j < 8; ++j) acc[0][j] = 0.0;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S) {
+        const int src = perm[i];
+        for (int j = 0; j < R / CT; ++j) {
+            const int c = cl + j * CT;
+            if (c < c0 || c >= c0 + k) continue;
+            const double v = B[(size_t)(c - c0) * n + src];
+            Bs[(size_t)i * R + c] = v;
+            acc[0][j] += v;
+        }
+    }
+    if (bcol_reduce<1, 8>(acc, R, CT, part, ticket, tot))
+        for (int c = threadIdx.x; c < R; c += kBThreads)
+            if (c >= c0 && c < c0 + k) col[c].bmean = tot[c] / (double)n;
+}
+
+// Centre the joining columns, r = Bs, x = 0 there, and start their CG.
+template <typename V>
+__global__ void __launch_bounds__(kBThreads)
+kb_join_center(int n, int R, int CT, int c0, int k, double *__restrict__ Bs, V *__restrict__ r,
+               V *__restrict__ x, BCol *col, double tol, int maxit, double *part, unsigned *ticket)
+{
+    __shared__ double tot[512];
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    double acc[2][8];
+    for (int j = 0; j < 8; ++j) acc[0][j] = acc[1][j] = 0.0;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S) {
+        for (int j = 0; j < R / CT; ++j) {
+            const int c = cl + j * CT;
+            if (c < c0 || c >= c0 + k) continue;
+            const size_t q = (size_t)i * R + c;
+            const double v = Bs[q] - col[c].bmean;
+            Bs[q] = v;
+            r[q] = (V)v;
+            x[q] = V(0);
+            acc[0][j] += v * v;
+            acc[1][j] += v;
+        }
+    }
+    if (bcol_reduce<2, 8>(acc, R, CT, part, ticket, tot)) {
+        for (int c = threadIdx.x; c < R; c += kBThreads) {
+            if (c < c0 || c >= c0 + k) continue;
+            BCol &C = col[c];
+            C.bnorm = sqrt(tot[c]);
+            C.rr = tot[c];
+            C.rs = tot[R + c];
+            C.relres = 1.0;
+            C.iter = 0;
+            C.first = 1;
+            C.tol = tol;
+            C.maxit = maxit;
+            C.join = 1;
+            C.flag = tot[c] > 0.0 ? kRun : kConverged;
+        }
+    }
+}
+
+// First direction of the joining columns only: p = z - zmean.
+template <typename V>
+__global__ void __launch_bounds__(kBThreads)
+kb_pupdate_join(int n, int R, int CT, const V *__restrict__ z, V *__restrict__ p, const BCol *col)
+{
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S)
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            if (col[c].join && col[c].flag == kRun) p[(size_t)i * R + c] = z[(size_t)i * R + c] - (V)col[c].zmean;
+        }
+}
+
+static __global__ void kb_clear_join(int R, BCol *col)
+{
+    for (int c = threadIdx.x; c < R; c += blockDim.x) col[c].join = 0;
+}
+
+// Stop columns [c0, c0 + k) (cancelled requests): flag := f.
+static __global__ void kb_set_flags(int R, int c0, int k, BCol *col, int f)
+{
+    for (int c = threadIdx.x; c < R; c += blockDim.x)
+        if (c >= c0 && c < c0 + k) col[c].flag = f;
+}
+
+// X(:, 0..k) = x(:, c0..c0+k) - mean, back in the caller's numbering.
+template <typename V>
+__global__ void __launch_bounds__(kBThreads)
+kb_scatter_range(int n, int R, int CT, int c0, int k, const int *__restrict__ perm,
+                 const V *__restrict__ x, const double *__restrict__ means, double *__restrict__ X)
+{
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S) {
+        const int dst = perm[i];
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            if (c >= c0 && c < c0 + k) X[(size_t)(c - c0) * n + dst] = (double)x[(size_t)i * R + c] - means[c];
         }
     }
 }

@@ -52,6 +52,7 @@ struct lap_handle_s {
     int hist_count = 0;
     int hist_capacity = 0;
     std::shared_ptr<lap::BatchWork> batch;   // allocated by the first batched solve
+    int batch_ct[6] = {0, 0, 0, 0, 0, 0};   // tuned column tile per batch width 8..256
 };
 
 namespace lap {

@@ -56,6 +56,15 @@ def parse():
     ap.add_argument("--nx", type=int, default=WORKLOAD["nx"], help="grid side (128 = the workload)")
     ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["pegp_inner", "msp", "none"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-scale", type=int, default=20,
+                    help="R-MAT scale of the batched line (0: skip it)")
+    ap.add_argument("--batched-rhs", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests of the serving line (0: skip it)")
+    ap.add_argument("--serve-graphs", type=int, default=32)
+    ap.add_argument("--serve-nmax", type=float, default=1e6)
+    ap.add_argument("--serve-plain-s", type=float, default=60.0,
+                    help="time limit of the plain FP64 comparison stream")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -67,6 +76,30 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def ranks_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world, device=None):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units per second of the whole job: every rank processed units_per_rank
+    (replicas), the job took the slowest rank's ms_max."""
+    return units_per_rank * world / (ms_max * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -218,8 +251,7 @@ def bench_ours(args, rank, world):
             inf = (P.lap_pcg_solve_host(hh, hB[i], xh) if host else P.lap_pcg_solve(hh, dB[i], x))
             print(f"[bench] warmup {precision} host={host}: {inf.as_dict()}", file=sys.stderr,
                   flush=True)
-        if world > 1:
-            torch.distributed.barrier()
+        ranks_barrier(world)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos, lat = [], []
@@ -235,13 +267,8 @@ def bench_ours(args, rank, world):
             lat.append((e_a, e_b))
         ev1.record(stream)
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ranks_barrier(world)
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
         lats = sorted(a.elapsed_time(b) for a, b in lat)
         return ms, infos, lats
 
@@ -281,17 +308,17 @@ def bench_ours(args, rank, world):
                          seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"], maxit=30000)
         ms_mm, inf_mm, lat_mm = timed("mixed", hh=hm, k_steps=A, w_steps=1)
         ms_mf, inf_mf, lat_mf = timed("fp64", hh=hm, k_steps=A, w_steps=0)
-        msp = {"mixed": {"value": A * world / (ms_mm * 1e-3), "unit": "solves/s",
+        msp = {"mixed": {"value": whole_job_rate(A, world, ms_mm), "unit": "solves/s",
                          "latency_ms": {"p50": pct(lat_mm, 0.5), "p99": pct(lat_mm, 0.99)},
                          "iterations": statistics.median(i.iterations for i in inf_mm)},
-               "fp64": {"value": A * world / (ms_mf * 1e-3), "unit": "solves/s",
+               "fp64": {"value": whole_job_rate(A, world, ms_mf), "unit": "solves/s",
                         "latency_ms": {"p50": pct(lat_mf, 0.5), "p99": pct(lat_mf, 0.99)},
                         "iterations": statistics.median(i.iterations for i in inf_mf)},
                "failed": [i.as_dict() for i in inf_mm + inf_mf if i.status != 0]}
         hm.close()
-    value = K * world / (ms_mixed * 1e-3)
-    fp64_value = A * world / (ms_fp64 * 1e-3)
-    e2e_value = A * world / (ms_e2e * 1e-3)
+    value = whole_job_rate(K, world, ms_mixed)
+    fp64_value = whole_job_rate(A, world, ms_fp64)
+    e2e_value = whole_job_rate(A, world, ms_e2e)
     it_mixed = statistics.median(i.iterations for i in inf_mixed)
     it_fp64 = statistics.median(i.iterations for i in inf_fp64)
     inner_fp64 = statistics.median(i.inner_iterations for i in inf_fp64)
@@ -328,13 +355,196 @@ def bench_ours(args, rank, world):
         "msp_same_system": msp,
         "failed_solves": failed,
     }
+    h.close()
+    if args.batched_scale > 0:
+        result["batched"] = bench_batched(args, dev, world)
+    if args.serve_requests > 0:
+        result["serving"] = bench_serving(args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             result["cpu_baseline"] = cpu_baseline(args.prec, g.n, it_fp64 + inner_fp64)
         except Exception as e:          # the baseline is reported, never fatal
             result["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
-    h.close()
     return result
+
+
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+
+def bench_batched(args, dev, world):
+    """Many right-hand sides at once: an R-MAT graph (scale s, edge factor 16,
+    a, b, c = 0.57, 0.19, 0.19, largest component, unit weights) with
+    `batched_rhs` N(0,1) columns solved together by lap_pcg_solve_batched (MSP,
+    mu = 0.8, FP32 SpMM and sweeps with per-column FP64 refinement), against
+    the plain FP64 single-solve path on a few of the same columns."""
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+    t0 = time.perf_counter()
+    g = gg.rmat(args.batched_scale, 16, seed=5)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h = P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                    tol=WORKLOAD["tol"], maxit=20000)
+    setup_s = time.perf_counter() - t0
+    k = args.batched_rhs
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(500)
+    B = torch.randn(k, g.n, dtype=torch.float64, device=dev, generator=gen)
+    X = torch.empty_like(B)
+    stream = torch.cuda.current_stream()
+    st, infos = P.lap_pcg_solve_batched([h], [B], [X])          # warm-up (autotune, graphs)
+    ranks_barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, infos = P.lap_pcg_solve_batched([h], [B], [X])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ranks_barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    bad = sum(1 for i in infos if i.status != 0)
+    # the plain FP64 single-solve path on the first columns
+    P.lap_update_options(h, precision="fp64")
+    ks = min(4, k)
+    x1 = torch.empty(g.n, dtype=torch.float64, device=dev)
+    P.lap_pcg_solve(h, B[0], x1)                                # warm-up
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    single = [P.lap_pcg_solve(h, B[j], x1) for j in range(ks)]
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = max_over_ranks(f0.elapsed_time(f1), world, dev)
+    info = P.lap_get_hierarchy_info(h)
+    h.close()
+    its = sorted(i.iterations for i in infos)
+    return {"workload": f"rmat_s{args.batched_scale}_ef16_unit_{k}rhs_MSP_mu0.8",
+            "n": g.n, "nnz": info["nnz"], "levels": info["levels"], "rhs": k,
+            "precision": "mixed (FP32 SpMM/sweeps, FP64 per-column refinement)",
+            "value": whole_job_rate(k, world, ms), "unit": "solves/s",
+            "ms_per_batch": ms, "iterations": {"median": its[len(its) // 2], "max": its[-1]},
+            "relres_max": max(i.relres for i in infos), "failed": bad,
+            "plain_fp64_single": {"value": whole_job_rate(ks, world, ms1), "unit": "solves/s",
+                                  "columns": ks,
+                                  "iterations": [i.iterations for i in single]},
+            "gen_s": round(gen_s, 2), "setup_s": round(setup_s, 2)}
+
+
+def _serving_graph(kind, n, rng, seed):
+    import graphgen as gg
+    w = dict(weights="loguniform", lo=1e-2, hi=1e2, seed=seed)
+    if kind == "grid2d":
+        return gg.grid2d(max(8, int(round(n ** 0.5))), **w)
+    if kind == "grid3d":
+        return gg.grid3d(max(4, int(round(n ** (1.0 / 3.0)))), **w)
+    if kind == "chung_lu":
+        return gg.chung_lu(int(n), avg_deg=float(rng.integers(8, 33)), **w)
+    return gg.rgg(int(n), avg_deg=10.0, **w)
+
+
+def bench_serving(args, dev, world):
+    """Continuous-batching server: `serve_graphs` resident graphs with vertex
+    counts log-uniform in [1e3, serve_nmax] (2D and 3D grids, Chung-Lu with
+    mean degree 8..32, random geometric graphs; weights log-uniform in
+    [1e-2, 1e2]), `serve_requests` requests of 1..16 N(0,1) right-hand sides
+    arriving as a Poisson stream at 70% of the server's measured capacity
+    (MSP, mu = 0.8, relres 1e-8).  The same stream (a prefix of it, within
+    a time limit) through the plain FP64 single-solve path for comparison."""
+    import numpy as np
+    import torch
+
+    import paper_2207_07847_gb300 as P
+    rng = np.random.default_rng(11)
+    G = args.serve_graphs
+    sizes = np.exp(rng.uniform(math.log(1e3), math.log(args.serve_nmax), G))
+    kinds = ["grid2d", "grid3d", "chung_lu", "rgg"]
+    t0 = time.perf_counter()
+    graphs = [_serving_graph(kinds[i % 4], sizes[i], rng, 300 + i) for i in range(G)]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs = [P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="fp64", seed=WORKLOAD["setup_seed"],
+                      tol=WORKLOAD["tol"], maxit=20000) for g in graphs]
+    setup_s = time.perf_counter() - t0
+    R = args.serve_requests
+    gi = rng.integers(0, G, R)
+    nr = rng.integers(1, 17, R)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(700)
+    Bs = [torch.randn(int(nr[i]), graphs[gi[i]].n, dtype=torch.float64, device=dev, generator=gen)
+          for i in range(R)]
+    Xs = [torch.empty_like(b) for b in Bs]
+    S = P.Server(max_slots=16, check_every=8, hbm_budget_bytes=96 << 30)
+
+    def run_stream(idx, arrivals):
+        """Submit requests idx at the given offsets (s); returns per-request
+        (latency s, status) and the wall time from first arrival to last completion."""
+        done = {}
+        ids = []
+        start = time.perf_counter()
+        for j, i in enumerate(idx):
+            delay = start + arrivals[j] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append((i, time.perf_counter(), S.submit(hs[gi[i]], Bs[i], Xs[i])))
+        last = start
+        for i, t_sub, rid in ids:
+            st, info = S.wait(rid, 600.0)
+            done[i] = (info.seconds, st)
+            last = max(last, t_sub + info.seconds)
+        return done, last - start
+
+    # capacity: a closed burst of the first requests
+    burst = list(range(min(64, R)))
+    _, t_burst = run_stream(burst, [0.0] * len(burst))
+    cap_rhs = float(sum(nr[i] for i in burst)) / t_burst
+    lam = 0.7 * cap_rhs / float(np.mean(nr))                 # requests per second
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, R))
+    arrivals -= arrivals[0]
+    ranks_barrier(world)
+    done, wall = run_stream(list(range(R)), arrivals)
+    S.close()
+    lat = [done[i][0] * 1e3 for i in range(R)]
+    failed = sum(1 for i in range(R) if done[i][1] != 0)
+    rhs_total = int(nr.sum())
+    wall = max_over_ranks(wall, world, dev)
+    # plain FP64 single solves of the same stream (prefix), FIFO, real time
+    plain_lat, plain_rhs = [], 0
+    x1 = {}
+    start = time.perf_counter()
+    for i in range(R):
+        now = time.perf_counter() - start
+        if now > args.serve_plain_s:
+            break
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        g = graphs[gi[i]]
+        if g.n not in x1:
+            x1[g.n] = torch.empty(g.n, dtype=torch.float64, device=dev)
+        for j in range(int(nr[i])):
+            P.lap_pcg_solve(hs[gi[i]], Bs[i][j], x1[g.n])
+        torch.cuda.synchronize()
+        plain_lat.append((time.perf_counter() - start - arrivals[i]) * 1e3)
+        plain_rhs += int(nr[i])
+    plain_wall = time.perf_counter() - start
+    for h in hs:
+        h.close()
+    return {"workload": f"serving_{G}graphs_n1e3..{args.serve_nmax:.0e}_{R}req_poisson",
+            "graphs": {"count": G, "n_min": int(min(g.n for g in graphs)),
+                       "n_max": int(max(g.n for g in graphs)), "kinds": kinds},
+            "requests": R, "rhs_total": rhs_total, "arrival_rate_req_s": round(lam, 2),
+            "precision": "fp64 columns, 16 per graph batch", "value": whole_job_rate(rhs_total, world, wall * 1e3),
+            "unit": "solves/s", "requests_per_s": R * world / wall,
+            "latency_ms": {"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99)}, "failed": failed,
+            "plain_fp64_single": {"requests": len(plain_lat), "rhs": plain_rhs,
+                                  "value": plain_rhs / plain_wall, "unit": "solves/s",
+                                  "latency_ms": {"p50": _pct(plain_lat, 0.5),
+                                                 "p99": _pct(plain_lat, 0.99)},
+                                  "time_limit_s": args.serve_plain_s},
+            "gen_s": round(gen_s, 2), "setup_s": round(setup_s, 2)}
 
 
 def bench_reference(args):

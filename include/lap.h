@@ -180,13 +180,16 @@ lap_status lap_update_options(lap_handle h, const lap_options *opts);
 /*
  * Time one kernel of the solve on the handle's data, for roofline reports:
  *   kernel 0: CSR matvec with L          kernel 1: CSR matvec with L_H (PEGP)
- *   kernel 2: the whole MSP sweep B r    kernel 3: fused CG update + level-1
- *                                                  restriction/elimination
+ *   kernel 2: the whole MSP sweep B r    kernel 3: fused CG update + the first
+ *                                                  upward band of the sweep
+ *   kernel 4: the sweep's coarse tail    kernel 5: the last downward band
+ *             (one block)                          (z and its reductions)
  * in FP64 (precision 0) or FP32 (precision 1, LAP_MIXED handles).  Runs `reps`
  * back-to-back launches (sequences for kernel 2) on the handle's stream
  * timed by CUDA events and writes the mean milliseconds per launch and the
  * algorithmic bytes of one launch (every array the kernel must touch, read
- * or written once).  Overwrites the handle's solve workspace.
+ * or written once).  Overwrites the handle's solve workspace.  Kernels 3-5
+ * need an MSP handle with at least two levels, else LAP_ERR_INVALID_ARG.
  */
 lap_status lap_kernel_bench(lap_handle h, int32_t kernel, int32_t precision, int32_t reps,
                             double *ms_per_launch, double *bytes_per_launch);

@@ -6,6 +6,7 @@
 #include <memory>
 #include <vector>
 
+#include "band.cuh"
 #include "kernels.cuh"
 #include "lap_internal.h"
 
@@ -28,7 +29,9 @@ struct DevBuf {
     bool alloc(size_t b)
     {
         reset();
-        if (b == 0) b = 16;
+        // 16-byte multiple plus 16 bytes: bulk copies of a range may round its
+        // end up to the next 16-byte boundary and read that far
+        b = (b + 15) / 16 * 16 + 16;
         p = dev_alloc(b, nullptr);
         bytes = p ? b : 0;
         return p != nullptr;
@@ -83,6 +86,11 @@ template <typename V> struct DevMsp {
     size_t tail_smem = 0;
     TailParams<V> tail_n{};            // n-space MSP (pc = 1, dcoef = c_k)
     TailParams<V> tail_t{};            // expanded-space solve (pc = dcoef = 1, f added)
+    // band sweeps of the levels below the tail, bottom band first; the three
+    // sets share their tiles and differ in coefficients
+    std::vector<BandParams<V>> band_n; // n-space MSP: gamma_k, dcoef c_k, pc 1
+    std::vector<BandParams<V>> band_t; // expanded-space solve: gamma 1, dcoef 1, pc 1
+    std::vector<BandParams<V>> band_p; // P(mu) by Horner: dcoef 1, pc -mu
 };
 
 // Reduction scratch + device scalars of one CG.

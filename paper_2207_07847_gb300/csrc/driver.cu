@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -138,6 +139,7 @@ lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, Dev
     return LAP_OK;
 }
 
+
 template <typename V>
 lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const DevMsp<double> *share)
 {
@@ -163,46 +165,200 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
     d.ntop = static_cast<int>(m.lev[l - 1].n);
     if (share) d.G = share->G;
     else LAP_TRY(upload(h, &d.G, m.coarse_pinv));
-    // fused tail: the deepest levels whose expanded size fits the shared-memory budget
-    const size_t budget = 200 * 1024;
+    // fused tail: the deepest levels whose values (twice), segments and
+    // coefficients fit the shared-memory budget, laid out as bulk copies
+    // need them (16-byte aligned, sizes rounded up)
+    const int budget = 200 * 1024;
+    const int sv = static_cast<int>(sizeof(V));
+    auto r16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+    auto tail_bytes = [&](int t) {
+        const int64_t ntl = m.offset[l] - m.offset[t];
+        int64_t b = r16(16 + ntl * sv) + r16(ntl * sv);
+        for (int k = t; k + 1 < l; ++k) {
+            const int64_t na = m.msp[k].nagg, nl = m.msp[k].n - 2 * na;
+            b += r16(4 * (na + 1)) + r16(4 * na * sv) + r16(3 * nl * sv);
+        }
+        return b;
+    };
     d.tail0 = -1;
     if (l >= 2) {
         for (int t = l - 1; t >= 1; --t) {
-            const int64_t nt = m.offset[l] - m.offset[t];
-            if (2 * nt * static_cast<int64_t>(sizeof(V)) > static_cast<int64_t>(budget) ||
-                l - 1 - t > kTailMaxLevels)
-                break;
+            if (tail_bytes(t) > budget || l - 1 - t > kTailMaxLevels) break;
             d.tail0 = t;
         }
     }
     if (d.tail0 >= 1) {
         const int t0 = d.tail0;
+        const int64_t ntl = m.offset[l] - m.offset[t0];
+        const int head0 = static_cast<int>((m.offset[t0] * sv) & 15);
+        int cur = 0;
+        const int sa_s = cur + head0;
+        cur += static_cast<int>(r16(head0 + ntl * sv));
+        const int sz_s = cur;
+        cur += static_cast<int>(r16(ntl * sv));
+        std::vector<std::array<int, 6>> lay(static_cast<size_t>(l - 1 - t0));
+        for (int k = 0; k < l - 1 - t0; ++k) {
+            const int64_t na = m.msp[t0 + k].nagg, nl = m.msp[t0 + k].n - 2 * na;
+            const int sb = static_cast<int>(r16(4 * (na + 1))), ib = static_cast<int>(r16(4 * na * sv)),
+                      lb = static_cast<int>(r16(3 * nl * sv));
+            lay[k] = {cur, sb, cur + sb, ib, cur + sb + ib, lb};
+            cur += sb + ib + lb;
+        }
         for (TailParams<V> *P : {&d.tail_n, &d.tail_t}) {
             const bool nspace = P == &d.tail_n;
             P->nlev = l - 1 - t0;
-            P->ntail = static_cast<int>(m.offset[l] - m.offset[t0]);
+            P->ntail = static_cast<int>(ntl);
             P->ntop = d.ntop;
             P->loc_top = static_cast<int>(m.offset[l - 1] - m.offset[t0]);
             P->off0 = m.offset[t0];
             P->n0 = static_cast<int>(m.lev[t0].n);
+            P->sa_s = sa_s;
+            P->sz_s = sz_s;
+            P->a0_head = head0;
+            P->smem = cur;
             P->G = d.G;
             P->top_scale = nspace ? m.c[l - 1] : 1.0;
             P->pc = V(1);
             P->write_all = nspace ? 0 : 1;
             for (int k = 0; k < P->nlev; ++k) {
                 const DevMspLevel<V> &Lk = d.lev[t0 + k];
-                P->lev[k].nagg = Lk.nagg;
-                P->lev[k].loc = static_cast<int>(m.offset[t0 + k] - m.offset[t0]);
-                P->lev[k].seg = Lk.seg;
-                P->lev[k].inv = Lk.inv;
-                P->lev[k].lcf = Lk.lcf;
-                P->lev[k].gamma = nspace ? d.gamma[t0 + k] : V(1);
-                P->lev[k].dcoef = nspace ? static_cast<V>(m.c[t0 + k]) : V(1);
+                TailLevel<V> &T = P->lev[k];
+                T.nagg = Lk.nagg;
+                T.loc = static_cast<int>(m.offset[t0 + k] - m.offset[t0]);
+                T.seg = Lk.seg;
+                T.inv = Lk.inv;
+                T.lcf = Lk.lcf;
+                T.seg_s = lay[k][0];
+                T.seg_b = lay[k][1];
+                T.inv_s = lay[k][2];
+                T.inv_b = lay[k][3];
+                T.lcf_s = lay[k][4];
+                T.lcf_b = lay[k][5];
+                T.gamma = nspace ? d.gamma[t0 + k] : V(1);
+                T.dcoef = nspace ? static_cast<V>(m.c[t0 + k]) : V(1);
             }
         }
-        d.tail_smem = static_cast<size_t>(2 * (m.offset[l] - m.offset[t0])) * sizeof(V);
-        LAP_CK(cudaFuncSetAttribute(k_msp_tail<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(budget)));
+        d.tail_smem = static_cast<size_t>(cur);
+        LAP_CK(cudaFuncSetAttribute(k_msp_tail<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget));
+        // the levels below the tail in bands
+        const int cap = kBandSmemBytes;
+        const std::vector<int> tops = plan_band_tops(m, t0, cap, sv);
+        int k0 = 0;
+        for (int k1 : tops) {
+            const int L = k1 - k0;
+            int ntiles = 0;
+            std::vector<int> tab;
+            std::vector<char> fits;
+            plan_band_tiles(m, k0, k1, cap, sv, tab, fits, ntiles);
+            // per tile: segments of all its levels as tile-local member
+            // offsets, then pair and leftover coefficients, one 16-byte
+            // aligned block; deltas get a 16-byte aligned block of the scratch
+            std::vector<unsigned char> coef;
+            std::vector<BandRec> rec(static_cast<size_t>(ntiles));
+            long long ds = 0;
+            auto put = [&](const void *src, size_t bytes) {
+                const auto *c = static_cast<const unsigned char *>(src);
+                coef.insert(coef.end(), c, c + bytes);
+            };
+            auto pad16 = [&]() { coef.resize((coef.size() + 15) / 16 * 16, 0); };
+            for (int t = 0; t < ntiles; ++t) {
+                const int *s0 = &tab[static_cast<size_t>(t) * (L + 1)];
+                const int *s1 = &tab[static_cast<size_t>(t + 1) * (L + 1)];
+                BandRec &R = rec[t];
+                R.cb = R.ds = 0;
+                R.cbytes = R.sbytes = -1;
+                if (!fits[t]) continue;
+                R.cb = static_cast<long long>(coef.size());
+                for (int j = 0; j < L; ++j) {
+                    const auto &S = m.msp[k0 + j];
+                    for (int J = s0[j + 1]; J <= s1[j + 1]; ++J) {
+                        const int32_t loc = S.seg[J] - s0[j];
+                        put(&loc, 4);
+                    }
+                }
+                pad16();
+                R.sbytes = static_cast<int>(coef.size() - R.cb);
+                for (int j = 0; j < L; ++j) {
+                    const auto &S = m.msp[k0 + j];
+                    for (int64_t i = 4ll * s0[j + 1]; i < 4ll * s1[j + 1]; ++i) {
+                        const V v = static_cast<V>(S.inv[i]);
+                        put(&v, sizeof(V));
+                    }
+                }
+                for (int j = 0; j < L; ++j) {
+                    const auto &S = m.msp[k0 + j];
+                    const int64_t l0 = 3ll * (s0[j] - 2ll * s0[j + 1]), l1 = 3ll * (s1[j] - 2ll * s1[j + 1]);
+                    for (int64_t i = l0; i < l1; ++i) {
+                        const V v = static_cast<V>(S.lcf[i]);
+                        put(&v, sizeof(V));
+                    }
+                }
+                pad16();
+                R.cbytes = static_cast<int>(coef.size() - R.cb);
+                R.ds = ds;
+                int64_t vals = 0;
+                for (int j = 0; j < L; ++j) vals += s1[j] - s0[j];
+                ds += (vals * sv + 15) / 16 * 16;
+            }
+            int *dtab = nullptr;
+            unsigned char *dcoef = nullptr;
+            BandRec *drec = nullptr;
+            LAP_TRY(upload(h, &dtab, tab));
+            LAP_TRY(upload(h, &dcoef, coef));
+            {
+                std::vector<unsigned char> raw(rec.size() * sizeof(BandRec));
+                std::memcpy(raw.data(), rec.data(), raw.size());
+                unsigned char *p = nullptr;
+                LAP_TRY(upload(h, &p, raw));
+                drec = reinterpret_cast<BandRec *>(p);
+            }
+            V *scratch = dalloc<V>(h, static_cast<size_t>(ds / sv + 1));
+            if (!scratch) return LAP_ERR_OOM;
+            BandParams<V> P{};
+            P.nlev = L;
+            P.ntiles = ntiles;
+            P.smem = kBandSmemBytes;
+            {
+                // one block per tile, at most what stays resident (the blocks
+                // then loop over the tiles)
+                for (const void *f : {(const void *)k_band_up<V, 0>, (const void *)k_band_up<V, 1>,
+                                      (const void *)k_band_up<V, 2>, (const void *)k_band_down<V, true, false>,
+                                      (const void *)k_band_down<V, false, false>,
+                                      (const void *)k_band_down<V, true, true>,
+                                      (const void *)k_band_down<V, false, true>})
+                    LAP_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes));
+                int occ_up = 0, occ_dn = 0;
+                LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_up, k_band_up<V, 1>, kBandThreads,
+                                                                     kBandSmemBytes));
+                LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_dn, k_band_down<V, true, false>,
+                                                                     kBandThreads, kBandSmemBytes));
+                auto grid = [&](int occ) {
+                    return std::max(1, std::min({ntiles, std::max(occ, 1) * h.sms, kMaxRedBlocks}));
+                };
+                P.grid_up = grid(occ_up);
+                P.grid_down = grid(occ_dn);
+            }
+            P.tstart = dtab;
+            P.rec = drec;
+            P.coef = dcoef;
+            P.scratch = scratch;
+            P.off_top = m.offset[k1];
+            P.pc = V(1);
+            for (int j = 0; j < P.nlev; ++j) {
+                const DevMspLevel<V> &Lk = d.lev[k0 + j];
+                P.lev[j] = BandLevel<V>{Lk.seg, Lk.inv, Lk.lcf, m.offset[k0 + j], d.gamma[k0 + j],
+                                        static_cast<V>(m.c[k0 + j])};
+            }
+            d.band_n.push_back(P);
+            for (int j = 0; j < P.nlev; ++j) {
+                P.lev[j].gamma = V(1);
+                P.lev[j].dcoef = V(1);
+            }
+            d.band_t.push_back(P);
+            P.pc = -d.mu;
+            d.band_p.push_back(P);
+            k0 = k1;
+        }
     }
     return LAP_OK;
 }
@@ -323,7 +479,10 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
 {
     const int n = static_cast<int>(M.off[1]);
     CgScalars *sc = st.sc;
-    h.launches += plain ? 1 : (M.levels == 1 ? 2 : 2 * ((M.tail0 >= 1 ? M.tail0 : M.levels - 1) - 1) + 3);
+    h.launches += plain ? 1
+                  : M.levels == 1 ? 2
+                  : !M.band_n.empty() ? static_cast<int64_t>(2 * M.band_n.size() + 1)
+                                      : 2 * ((M.tail0 >= 1 ? M.tail0 : M.levels - 1) - 1) + 3;
     if (plain || M.levels == 1) {
         const int g = grid_for(h, n);
 #define LAP_UPD(U, P) \
@@ -339,6 +498,40 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
         return;
     }
     const int l = M.levels;
+    if (!M.band_n.empty()) {
+        // levels below the tail in bands (one launch per band and direction),
+        // the tail in one block
+        const size_t nb = M.band_n.size();
+        for (size_t b = 0; b < nb; ++b) {
+            const BandParams<V> &P = M.band_n[b];
+            const size_t sm = static_cast<size_t>(P.smem);
+            if (b > 0)
+                k_band_up<V, 0><<<P.grid_up, kBandThreads, sm, s>>>(P, nullptr, nullptr, nullptr, nullptr,
+                                                                      w.A, nullptr, sc, nullptr, nullptr);
+            else if (update)
+                k_band_up<V, 1><<<P.grid_up, kBandThreads, sm, s>>>(P, w.x, w.r, w.p, w.q, w.A, nullptr, sc,
+                                                                      st.part, st.ticket);
+            else
+                k_band_up<V, 2><<<P.grid_up, kBandThreads, sm, s>>>(P, w.x, w.r, w.p, w.q, w.A, nullptr, sc,
+                                                                      st.part, st.ticket);
+        }
+        TailParams<V> T = M.tail_n;
+        T.A = w.A;
+        T.Y = w.Y;
+        T.F = nullptr;
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, sc);
+        for (size_t b = nb; b-- > 0;) {
+            const BandParams<V> &P = M.band_n[b];
+            const size_t sm = static_cast<size_t>(P.smem);
+            if (b == 0)
+                k_band_down<V, true, false><<<P.grid_down, kBandThreads, sm, s>>>(P, w.A, w.Y, w.Y, w.z, 0, n, w.r,
+                                                                           w.q, sc, st.part, st.ticket);
+            else
+                k_band_down<V, false, false><<<P.grid_down, kBandThreads, sm, s>>>(
+                    P, w.A, w.Y, w.Y, w.Y + P.lev[0].off, 0, n, nullptr, nullptr, sc, nullptr, nullptr);
+        }
+        return;
+    }
     const auto &L0 = M.lev[0];
     if (update)
         k_up_tiled<V, 1><<<grid_for(h, L0.nagg), kTA, 0, s>>>(
@@ -394,6 +587,29 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
                cudaStream_t s)
 {
     const int l = M.levels;
+    if (!M.band_t.empty()) {
+        // bands below the tail (f added on restriction), the tail, bands down;
+        // every level of Y is written
+        const size_t nb = M.band_t.size();
+        h.launches += static_cast<int64_t>(2 * nb + 1);
+        CgScalars *scm = const_cast<CgScalars *>(sc);
+        for (size_t b = 0; b < nb; ++b) {
+            const BandParams<V> &P = M.band_t[b];
+            k_band_up<V, 0><<<P.grid_up, kBandThreads, static_cast<size_t>(P.smem), s>>>(
+                P, nullptr, nullptr, nullptr, nullptr, A, A, scm, nullptr, nullptr);
+        }
+        TailParams<V> T = M.tail_t;
+        T.A = A;
+        T.Y = Y;
+        T.F = A;
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, sc);
+        for (size_t b = nb; b-- > 0;) {
+            const BandParams<V> &P = M.band_t[b];
+            k_band_down<V, false, false><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
+                P, A, Y, Y, Y + P.lev[0].off, 1, 0, nullptr, nullptr, scm, nullptr, nullptr);
+        }
+        return;
+    }
     const int t0 = M.tail0 >= 0 ? std::max(M.tail0, 0) : l - 1;
     const int up_end = M.tail0 >= 1 ? t0 : l - 1;
     h.launches += 2 * up_end + 1;
@@ -453,6 +669,31 @@ void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, 
 {
     const int l = M.levels;
     const int64_t ot = M.off[l - 1];
+    if (!M.band_p.empty()) {
+        // per level from the top down to the tail's first level, then the bands
+        const int t0 = M.tail0;
+        const size_t nb = M.band_p.size();
+        h.launches += 1 + (l - 1 - t0) + static_cast<int64_t>(nb);
+        k_copy2<V><<<grid_for(h, M.ntop), kBlock, 0, s>>>(M.ntop, yt + ot, T + ot, nullptr, st.sc);
+        for (int k = l - 2; k >= t0; --k) {
+            const auto &Lk = M.lev[k];
+            k_down_tiled<V, false><<<grid_for(h, Lk.nagg), kTA, 0, s>>>(
+                Lk.n, Lk.nagg, Lk.seg, yt + M.off[k], T + M.off[k + 1], T + M.off[k], -M.mu, V(1), nullptr,
+                nullptr, st.sc, nullptr, nullptr);
+        }
+        const int n = static_cast<int>(M.off[1]);
+        for (size_t b = nb; b-- > 0;) {
+            const BandParams<V> &P = M.band_p[b];
+            const size_t sm = static_cast<size_t>(P.smem);
+            if (b == 0)
+                k_band_down<V, true, true><<<P.grid_down, kBandThreads, sm, s>>>(P, yt, T, T, w.z, 0, n, w.r,
+                                                                                 w.q, st.sc, st.part, st.ticket);
+            else
+                k_band_down<V, false, true><<<P.grid_down, kBandThreads, sm, s>>>(
+                    P, yt, T, T, T + P.lev[0].off, 0, n, nullptr, nullptr, st.sc, nullptr, nullptr);
+        }
+        return;
+    }
     h.launches += l;
     k_copy2<V><<<grid_for(h, M.ntop), kBlock, 0, s>>>(M.ntop, yt + ot, T + ot, nullptr, st.sc);
     for (int k = l - 2; k >= 1; --k) {
@@ -1105,23 +1346,37 @@ namespace {
 template <typename V>
 double sweep_bytes(const DevMsp<V> &M)
 {
-    // MSP sweep B r, every array touched once: level 1 reads r, writes delta_1,
-    // reads segments / pair and leftover coefficients and writes a_2; levels
-    // 2..l-1 update a_k in place; the top level reads a_l and G; the way down
-    // reads delta_k and the parents' accumulated value and writes its own
-    // (level 1: reads r and writes z).
+    // MSP sweep z = B r, every array moved once: r read and z written (n
+    // values each), each level's segments and elimination coefficients read
+    // once, every level's deltas stored on the way up and read on the way
+    // down, and the top level's dense pseudo-inverse read.  Intermediate
+    // restrictions and prolongations need no memory traffic of their own.
     const double s = sizeof(V);
-    double b = 0.0;
     const int l = M.levels;
+    double b = 2.0 * s * static_cast<double>(M.off[1]);
     for (int k = 0; k + 1 < l; ++k) {
         const double n = M.lev[k].n, na = M.lev[k].nagg, nl = n - 2 * na;
-        const double seg = 4.0 * (na + 1), coef = s * (4 * na + 3 * nl);
-        const double up = 2 * s * n + seg + coef + s * na;
-        const double down = k == 0 ? (s * n /*delta*/ + s * na + s * n /*r*/ + s * n /*z*/ + seg)
-                                   : (s * n + s * na + s * n + seg);
-        b += up + down;
+        b += 4.0 * (na + 1) + s * (4 * na + 3 * nl) + 2.0 * s * n;
     }
-    b += 8.0 * M.ntop * M.ntop + 3 * s * M.ntop;
+    b += 8.0 * M.ntop * M.ntop;
+    return b;
+}
+
+// Algorithmic bytes of the first upward band with the CG step fused: x, p, q,
+// r read and x, r written, the band's coefficients read, its deltas and the
+// next level's right-hand side written.
+template <typename V>
+double band_up_bytes(const DevMsp<V> &M)
+{
+    const double s = sizeof(V);
+    const BandParams<V> &P = M.band_n[0];
+    const int k1 = P.nlev;
+    double b = 6.0 * s * static_cast<double>(M.off[1]);
+    for (int k = 0; k < k1; ++k) {
+        const double n = M.lev[k].n, na = M.lev[k].nagg, nl = n - 2 * na;
+        b += 4.0 * (na + 1) + s * (4 * na + 3 * nl) + (k > 0 ? s * n : 0.0);
+    }
+    b += s * static_cast<double>(M.off[k1 + 1] - M.off[k1]);
     return b;
 }
 }  // namespace
@@ -1130,7 +1385,7 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
 {
     if (precision == 1 && !h.L32.w) return LAP_ERR_INVALID_ARG;
     if (kernel == 1 && !h.H64.w) return LAP_ERR_INVALID_ARG;
-    if (kernel < 0 || kernel > 3) return LAP_ERR_INVALID_ARG;
+    if (kernel < 0 || kernel > 5) return LAP_ERR_INVALID_ARG;
     const cudaStream_t s = h.s;
     cudaEvent_t e0, e1;
     LAP_CK(cudaEventCreate(&e0));
@@ -1148,10 +1403,26 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
             case 1: spmv<V, 2>(h, Sel<V>::H(h), h.tprH, Sel<V>::e(h).p, Sel<V>::e(h).q, nullptr,
                                nullptr, h.stb, s); break;
             case 2: precond_msp<V>(h, M, w, h.stb, false, false, s); break;
-            default:
-                k_up_tiled<V, 1><<<grid_for(h, M.lev[0].nagg), kTA, 0, s>>>(
-                    M.lev[0].nagg, M.lev[0].seg, M.lev[0].inv, M.lev[0].lcf, w.x, w.r, w.p, w.q, w.A,
-                    w.A + M.off[1], M.gamma[0], nullptr, h.stb.sc, h.stb.part, h.stb.ticket);
+            case 3: {
+                const BandParams<V> &P = M.band_n[0];
+                k_band_up<V, 1><<<P.grid_up, kBandThreads, static_cast<size_t>(P.smem), s>>>(
+                    P, w.x, w.r, w.p, w.q, w.A, nullptr, h.stb.sc, h.stb.part, h.stb.ticket);
+                break;
+            }
+            case 4: {
+                TailParams<V> T = M.tail_n;
+                T.A = w.A;
+                T.Y = w.Y;
+                T.F = nullptr;
+                k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, h.stb.sc);
+                break;
+            }
+            default: {
+                const BandParams<V> &P = M.band_n[0];
+                k_band_down<V, true, false><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
+                    P, w.A, w.Y, w.Y, w.z, 0, static_cast<int>(n), w.r, w.q, h.stb.sc, h.stb.part,
+                    h.stb.ticket);
+            }
             }
         };
         const double sv = sizeof(V);
@@ -1160,11 +1431,28 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
             by = A.nnz * (4.0 + sv) + 4.0 * (A.n + 1) + 2.0 * sv * A.n;
         } else if (kernel == 2) {
             by = sweep_bytes(M);
+        } else if (kernel == 3) {
+            if (M.band_n.empty()) return -1.0;
+            by = band_up_bytes(M);
+        } else if (kernel == 4) {
+            if (M.tail0 < 1) return -1.0;
+            // the tail's levels: values read and written, coefficients and the
+            // top pseudo-inverse read once
+            const int l = M.levels;
+            by = 2.0 * sv * static_cast<double>(M.off[l] - M.off[M.tail0]) + 8.0 * M.ntop * M.ntop;
+            for (int k = M.tail0; k + 1 < l; ++k) {
+                const double nk = M.lev[k].n, na = M.lev[k].nagg;
+                by += 4.0 * (na + 1) + sv * (4 * na + 3 * (nk - 2 * na));
+            }
         } else {
-            const double na = M.lev[0].nagg, nl = n - 2 * na;
-            by = 6.0 * sv * n + sv * n + 4.0 * (na + 1) + sv * (4 * na + 3 * nl) + sv * na;
+            if (M.band_n.empty()) return -1.0;
+            // first band down: deltas and segments of its levels read, the
+            // parents read, z written, r read for the reductions
+            const BandParams<V> &P = M.band_n[0];
+            by = 2.0 * sv * static_cast<double>(n);
+            for (int k = 0; k < P.nlev; ++k) by += sv * M.lev[k].n + 4.0 * (M.lev[k].nagg + 1);
+            by += sv * static_cast<double>(M.off[P.nlev + 1] - M.off[P.nlev]);
         }
-        if (kernel == 3 && M.levels < 2) return -1.0;
         launch();                                   // warm-up
         cudaEventRecord(e0, s);
         for (int i = 0; i < reps; ++i) launch();

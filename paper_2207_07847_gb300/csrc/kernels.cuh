@@ -59,7 +59,7 @@ enum : int { kRun = 0, kConverged = 1, kBreakdown = 2, kMaxit = 3 };
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV])
 {
-    __shared__ double sm[kBlock / 32][NV];
+    __shared__ double sm[32][NV];              // blocks of up to 1024 threads
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
@@ -541,9 +541,11 @@ k_down_tiled(int n, int nagg, const int *__restrict__ seg, const V *__restrict__
 
 // ---------------------------------------------------------------------------
 // Fused coarse tail of the sweep: levels t0..l (0-based t0 >= 1) whose
-// expanded size fits in shared memory are restricted + eliminated upwards,
-// solved on top and prolongated downwards by ONE block, with a barrier per
-// level instead of a kernel launch per level.
+// values, segments and elimination coefficients all fit in shared memory are
+// restricted + eliminated upwards, solved on top and prolongated downwards by
+// ONE block, with a barrier per level instead of a kernel launch per level.
+// Everything is brought in at the start by bulk copies (one per array, in
+// flight together); the shared-memory layout is computed at setup.
 // ---------------------------------------------------------------------------
 constexpr int kTailMaxLevels = LAP_TAIL_MAX_LEVELS;
 
@@ -553,6 +555,8 @@ template <typename V> struct TailLevel {
     const int *seg;
     const V *inv;
     const V *lcf;
+    int seg_s, inv_s, lcf_s;  // byte offsets of the staged copies in shared memory
+    int seg_b, inv_b, lcf_b;  // bytes copied (16-byte multiples, 0: none)
     V gamma;                  // restriction factor to the next level
     V dcoef;                  // down pass: out = pc * parent + dcoef * delta
 };
@@ -563,6 +567,9 @@ template <typename V> struct TailParams {
     int ntop, loc_top;
     int64_t off0;             // expanded offset of the tail's first level
     int n0;                   // vertices of the tail's first level
+    int sa_s, sz_s;           // byte offsets of the value arrays (sa: after its 16-byte head)
+    int a0_head;              // bytes between the copy of A's first tail level and sa
+    int smem;                 // shared-memory bytes of the launch
     const double *G;
     double top_scale;
     V pc;
@@ -579,20 +586,65 @@ k_msp_tail(const TailParams<V> P, const CgScalars *sc)
 {
     if (halted(sc)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *sa = reinterpret_cast<V *>(smem_raw);
-    V *sz = sa + P.ntail;
+    __shared__ __align__(8) uint64_t bar;
+    V *sa = reinterpret_cast<V *>(smem_raw + P.sa_s);
+    V *sz = reinterpret_cast<V *>(smem_raw + P.sz_s);
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < P.n0; i += nth) sa[i] = P.A[P.off0 + i];
+    if (tid == 0) {
+        const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const int a0_bytes = (P.a0_head + P.n0 * (int)sizeof(V) + 15) & ~15;
+        uint32_t tx = a0_bytes;
+        for (int k = 0; k < P.nlev; ++k) tx += P.lev[k].seg_b + P.lev[k].inv_b + P.lev[k].lcf_b;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(tx) : "memory");
+        auto copy = [&](int dst, const void *src, int bytes) {
+            if (bytes <= 0) return;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw + dst))),
+                "l"(src), "r"(bytes), "r"(b)
+                : "memory");
+        };
+        copy(P.sa_s - P.a0_head, reinterpret_cast<const unsigned char *>(P.A + P.off0) - P.a0_head, a0_bytes);
+        for (int k = 0; k < P.nlev; ++k) {
+            const TailLevel<V> &L = P.lev[k];
+            copy(L.seg_s, L.seg, L.seg_b);
+            copy(L.inv_s, L.inv, L.inv_b);
+            copy(L.lcf_s, L.lcf, L.lcf_b);
+        }
+    }
     __syncthreads();
+    {
+        const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+        const long long t0 = clock64();
+        for (;;) {
+            uint32_t done;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(b)
+                : "memory");
+            if (done) break;
+            if (clock64() - t0 > (1ll << 31)) {          // about a second: give up, flag it
+                if (tid == 0 && sc) const_cast<CgScalars *>(sc)->flag = kBreakdown;
+                return;
+            }
+        }
+    }
     for (int k = 0; k < P.nlev; ++k) {
         const TailLevel<V> &L = P.lev[k];
         V *a = sa + L.loc;
+        const int *seg = reinterpret_cast<const int *>(smem_raw + L.seg_s);
+        const V *inv = reinterpret_cast<const V *>(smem_raw + L.inv_s);
+        const V *lcf = reinterpret_cast<const V *>(smem_raw + L.lcf_s);
         const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
         for (int J = tid; J < L.nagg; J += nth) {
-            const int b0 = L.seg[J], e = L.seg[J + 1];
+            const int b0 = seg[J], e = seg[J + 1];
             const V aa = a[b0], ab = a[b0 + 1];
             V sum = aa + ab, ha = aa, hb = ab;
-            const V *lc = L.lcf + 3 * (b0 - 2 * J);
+            const V *lc = lcf + 3 * (b0 - 2 * J);
             for (int t = b0 + 2; t < e; ++t) {
                 const V al = a[t];
                 const V *c = lc + 3 * (t - b0 - 2);
@@ -601,7 +653,7 @@ k_msp_tail(const TailParams<V> P, const CgScalars *sc)
                 hb += c[1] * al;
             }
             V da, db;
-            pair_solve(L.inv + 4 * J, ha, hb, da, db);
+            pair_solve(inv + 4 * J, ha, hb, da, db);
             for (int t = b0 + 2; t < e; ++t) {
                 const V *c = lc + 3 * (t - b0 - 2);
                 a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
@@ -628,10 +680,11 @@ k_msp_tail(const TailParams<V> P, const CgScalars *sc)
     __syncthreads();
     for (int k = P.nlev - 1; k >= 0; --k) {
         const TailLevel<V> &L = P.lev[k];
+        const int *seg = reinterpret_cast<const int *>(smem_raw + L.seg_s);
         const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
         for (int J = tid; J < L.nagg; J += nth) {
             const V base = P.pc * sz[nloc + J];
-            for (int u = L.seg[J]; u < L.seg[J + 1]; ++u) sz[L.loc + u] = base + L.dcoef * sa[L.loc + u];
+            for (int u = seg[J]; u < seg[J + 1]; ++u) sz[L.loc + u] = base + L.dcoef * sa[L.loc + u];
         }
         __syncthreads();
     }

@@ -662,4 +662,109 @@ void expanded_edges(const HostModel &m, int which, std::vector<int64_t> &I,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Band planning (setup).  start[j][P] is the first level-(k0+j) descendant of
+// level-k1 vertex P in tree order (start[j][N] = n_{k0+j}): seg of each level
+// maps the first aggregate of a range to its first member.
+static std::vector<std::vector<int64_t>> band_starts(const HostModel &m, int k0, int k1)
+{
+    const int L = k1 - k0;
+    const int64_t N = m.lev[k1].n;
+    std::vector<std::vector<int64_t>> start(static_cast<size_t>(L + 1));
+    start[L].resize(static_cast<size_t>(N + 1));
+    for (int64_t P = 0; P <= N; ++P) start[L][P] = P;
+    for (int j = L - 1; j >= 0; --j) {
+        const auto &seg = m.msp[k0 + j].seg;
+        start[j].resize(static_cast<size_t>(N + 1));
+        for (int64_t P = 0; P <= N; ++P) start[j][P] = seg[start[j + 1][P]];
+    }
+    return start;
+}
+
+// Shared-memory bytes of a tile holding the level-k1 vertices [a, b) with
+// values of sv bytes: the largest of its upward layout (packed segments and
+// coefficients, then the values of every level), its downward layout
+// (segments, the deltas of levels k0..k1-1, the level-k1 values and r of the
+// finest level) and the downward layout with deltas read level by level from
+// an expanded array.
+// Every range copied from global memory is rounded out to 16 bytes.
+static int64_t band_need(const std::vector<std::vector<int64_t>> &start, int64_t a, int64_t b, int sv)
+{
+    const int L = static_cast<int>(start.size()) - 1;
+    auto r16 = [](int64_t x) { return (x + 15) / 16 * 16; };
+    std::vector<int64_t> c(static_cast<size_t>(L + 1));
+    for (int j = 0; j <= L; ++j) c[j] = start[j][b] - start[j][a];
+    int64_t segs = 0, coefs = 0, vals_up = 0, vals_dn = 0, dx = 0;
+    for (int j = 0; j < L; ++j) {
+        segs += c[j + 1] + 1;
+        coefs += 4 * c[j + 1] + 3 * (c[j] - 2 * c[j + 1]);
+        vals_dn += c[j];
+        dx += r16(16 + c[j] * sv);
+    }
+    for (int j = 1; j <= L; ++j) vals_up += c[j];
+    const int64_t seg_bytes = r16(4 * segs);
+    const int64_t up = seg_bytes + r16(coefs * sv) + r16(16 + c[0] * sv) + r16(vals_up * sv);
+    const int64_t par = r16(16 + c[L] * sv), rfin = r16(16 + c[0] * sv);
+    const int64_t down = seg_bytes + r16(vals_dn * sv) + par + rfin;
+    const int64_t downx = seg_bytes + dx + par + rfin;
+    return std::max(up, std::max(down, downx));
+}
+
+// Band tops: from level 0 up, the highest k1 <= min(kmax, k0 + kBandMaxLevels)
+// whose oversized subtrees (more than `cap` bytes, run in global memory)
+// hold at most a tenth of the band's values; at least one level per band.
+std::vector<int> plan_band_tops(const HostModel &m, int kmax, int cap, int sv)
+{
+    std::vector<int> tops;
+    int k0 = 0;
+    while (k0 < kmax) {
+        int best = k0 + 1;
+        for (int k1 = std::min(kmax, k0 + kBandMaxLevels); k1 > k0 + 1; --k1) {
+            const auto start = band_starts(m, k0, k1);
+            const int64_t N = m.lev[k1].n;
+            int64_t big = 0, all = 0;
+            for (int64_t P = 0; P < N; ++P) {
+                int64_t v = 0;
+                for (const auto &st : start) v += st[P + 1] - st[P];
+                all += v;
+                if (band_need(start, P, P + 1, sv) > cap) big += v;
+            }
+            if (10 * big <= all) {
+                best = k1;
+                break;
+            }
+        }
+        tops.push_back(best);
+        k0 = best;
+    }
+    return tops;
+}
+
+// Tiles of band [k0, k1): runs of consecutive level-k1 vertices that fit
+// `cap` bytes (one vertex at least).  tab: ntiles + 1 rows of the L + 1 first
+// indices; fits: per tile, whether it fits (else it runs in global memory).
+void plan_band_tiles(const HostModel &m, int k0, int k1, int cap, int sv, std::vector<int> &tab,
+                     std::vector<char> &fits, int &ntiles)
+{
+    const int L = k1 - k0;
+    const auto start = band_starts(m, k0, k1);
+    const int64_t N = m.lev[k1].n;
+    tab.clear();
+    fits.clear();
+    auto push = [&](int64_t P) {
+        for (int j = 0; j <= L; ++j) tab.push_back(static_cast<int>(start[j][P]));
+    };
+    push(0);
+    ntiles = 0;
+    for (int64_t P0 = 0; P0 < N;) {
+        int64_t P1 = P0 + 1;
+        while (P1 < N && band_need(start, P0, P1 + 1, sv) <= cap) ++P1;
+        fits.push_back(band_need(start, P0, P1, sv) <= cap ? 1 : 0);
+        push(P1);
+        ++ntiles;
+        P0 = P1;
+    }
+}
+
+
 }  // namespace lap

@@ -209,8 +209,9 @@ __device__ __forceinline__ void band_up_level(const BandParams<V> &P, const Band
 // in A for a tile in global memory) and the accumulated right-hand side of
 // level k1 written to A.
 // MODE 1: k0 = 0 with the CG step (x += alpha p, r -= alpha q), a_0 = r,
-//         reductions ||r||^2, sum r and the convergence test;
-// MODE 2: k0 = 0, a_0 = r, the same reductions without the step;
+//         per-block partials of ||r||^2, sum r to part[2 b], part[2 b + 1]
+//         (finished by the coarse tail: the convergence test);
+// MODE 2: k0 = 0, a_0 = r, the same partials without the step;
 // MODE 0: a_{k0} read from A.
 // F (optional): expanded right-hand side added on restriction (a_{k+1} +=
 // F_{k+1}; may alias A, read before it is overwritten).
@@ -236,6 +237,9 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
         __syncthreads();
         const int64_t o0 = P.lev[0].off;
         if (T.rec.cbytes >= 0) {
+            // thread 0 lays the tile out and starts the copies while the
+            // block takes level 0 from r (MODE 1, 2) into the region after
+            // the coefficients
             if (tid == 0) {
                 band_coef_offsets<V>(L, T);
                 // coefficients at 0, level-0 values after them (with the
@@ -253,10 +257,9 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
                 bulk_load(band_raw, P.coef + T.rec.cb, T.rec.cbytes, &bar);
                 if (MODE == 0) bulk_load(band_raw + u0, s0.src, s0.bytes, &bar);
             }
-            __syncthreads();
             if (MODE != 0) {
                 // level 0 from r (after the CG step), four elements per thread in flight
-                V *v0 = reinterpret_cast<V *>(band_raw + T.vs[0]);
+                V *v0 = reinterpret_cast<V *>(band_raw + T.rec.cbytes);
                 for (int i0 = tid; i0 < T.cnt[0]; i0 += 4 * kBandThreads) {
                     V xv[4], pv[4], qv[4], rv[4];
 #pragma unroll
@@ -377,20 +380,15 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
         __syncthreads();
     }
     if (MODE == 0) return;
+    // per-block partials of ||r||^2 and sum r; the next single-block kernel
+    // (the coarse tail) adds them up and finishes the iteration's test
     double v[2] = {rr, rs};
-    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
-        sc->rr = v[0];
-        sc->rs = v[1];
-        if (MODE == 1) {
-            sc->iter += 1;
-            const double rel = sqrt(v[0]) / sc->bnorm;
-            sc->relres = rel;
-            if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
-            if (!isfinite(rel)) sc->flag = kBreakdown;
-            else if (rel <= sc->tol) sc->flag = kConverged;
-            else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
-        }
+    block_sum<2>(v);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = v[0];
+        part[2 * blockIdx.x + 1] = v[1];
     }
+    (void)ticket;
 }
 
 // One level of the downward pass for aggregates jl = first, first + step, ...

@@ -243,13 +243,46 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
         // the levels below the tail in bands
         const int cap = kBandSmemBytes;
         const std::vector<int> tops = plan_band_tops(m, t0, cap, sv);
+        // resident band blocks: the grid, and the unit the tile count is balanced to
+        for (const void *f : {(const void *)k_band_up<V, 0>, (const void *)k_band_up<V, 1>,
+                              (const void *)k_band_up<V, 2>, (const void *)k_band_down<V, true, false>,
+                              (const void *)k_band_down<V, false, false>, (const void *)k_band_down<V, true, true>,
+                              (const void *)k_band_down<V, false, true>})
+            LAP_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes));
+        int occ_up = 0, occ_dn = 0;
+        LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_up, k_band_up<V, 1>, kBandThreads, kBandSmemBytes));
+        LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_dn, k_band_down<V, true, false>, kBandThreads,
+                                                             kBandSmemBytes));
+        const int resident = std::max(1, std::min(occ_up, occ_dn)) * h.sms;
         int k0 = 0;
         for (int k1 : tops) {
             const int L = k1 - k0;
             int ntiles = 0;
             std::vector<int> tab;
             std::vector<char> fits;
-            plan_band_tiles(m, k0, k1, cap, sv, tab, fits, ntiles);
+            plan_band_tiles(m, k0, k1, cap, cap, sv, tab, fits, ntiles);
+            if (ntiles > resident && resident < kMaxRedBlocks) {
+                // every block loops over the same number of tiles: shrink the
+                // tiles until the count reaches the next multiple of the
+                // resident blocks, then grow them back just under it
+                const int waves = (ntiles + resident - 1) / resident;
+                const int want = waves * resident;
+                int c = static_cast<int>(static_cast<int64_t>(cap) * ntiles / want);
+                for (int it = 0; it < 40; ++it) {
+                    int nt2 = 0;
+                    std::vector<int> tab2;
+                    std::vector<char> fits2;
+                    plan_band_tiles(m, k0, k1, c, cap, sv, tab2, fits2, nt2);
+                    if (nt2 <= want) {
+                        tab.swap(tab2);
+                        fits.swap(fits2);
+                        ntiles = nt2;
+                        break;
+                    }
+                    c += std::max(16, c / 50);
+                    if (c >= cap) break;
+                }
+            }
             // per tile: segments of all its levels as tile-local member
             // offsets, then pair and leftover coefficients, one 16-byte
             // aligned block; deltas get a 16-byte aligned block of the scratch
@@ -318,26 +351,9 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
             P.nlev = L;
             P.ntiles = ntiles;
             P.smem = kBandSmemBytes;
-            {
-                // one block per tile, at most what stays resident (the blocks
-                // then loop over the tiles)
-                for (const void *f : {(const void *)k_band_up<V, 0>, (const void *)k_band_up<V, 1>,
-                                      (const void *)k_band_up<V, 2>, (const void *)k_band_down<V, true, false>,
-                                      (const void *)k_band_down<V, false, false>,
-                                      (const void *)k_band_down<V, true, true>,
-                                      (const void *)k_band_down<V, false, true>})
-                    LAP_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes));
-                int occ_up = 0, occ_dn = 0;
-                LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_up, k_band_up<V, 1>, kBandThreads,
-                                                                     kBandSmemBytes));
-                LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_dn, k_band_down<V, true, false>,
-                                                                     kBandThreads, kBandSmemBytes));
-                auto grid = [&](int occ) {
-                    return std::max(1, std::min({ntiles, std::max(occ, 1) * h.sms, kMaxRedBlocks}));
-                };
-                P.grid_up = grid(occ_up);
-                P.grid_down = grid(occ_dn);
-            }
+            // one block per tile, at most what stays resident (the blocks then
+            // loop over the tiles)
+            P.grid_up = P.grid_down = std::max(1, std::min({ntiles, resident, kMaxRedBlocks}));
             P.tstart = dtab;
             P.rec = drec;
             P.coef = dcoef;
@@ -519,6 +535,9 @@ void precond_msp(const lap_handle_s &h, const DevMsp<V> &M, const CgVectors<V> &
         T.A = w.A;
         T.Y = w.Y;
         T.F = nullptr;
+        T.fin = update ? 1 : 2;                  // the first band's reductions
+        T.fin_n = M.band_n[0].grid_up;
+        T.fin_part = st.part;
         k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, sc);
         for (size_t b = nb; b-- > 0;) {
             const BandParams<V> &P = M.band_n[b];
@@ -602,7 +621,7 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
         T.A = A;
         T.Y = Y;
         T.F = A;
-        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, sc);
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, scm);
         for (size_t b = nb; b-- > 0;) {
             const BandParams<V> &P = M.band_t[b];
             k_band_down<V, false, false><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
@@ -625,7 +644,7 @@ void msp_tilde(const lap_handle_s &h, const DevMsp<V> &M, V *A, V *Y, const CgSc
         P.A = A;
         P.Y = Y;
         P.F = A;
-        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(P, sc);
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(P, const_cast<CgScalars *>(sc));
     } else {
         const int64_t ot = M.off[l - 1];
         k_coarse<V><<<grid_for(h, int64_t(M.ntop) * 32), kBlock, 0, s>>>(M.ntop, M.G, A + ot, Y + ot,

@@ -577,16 +577,47 @@ template <typename V> struct TailParams {
     V *Y;                     // global output (expanded, tree order)
     const V *F;               // expanded right-hand side added on restriction, or null
     int write_all;            // write every tail level of Y (else the first only)
+    // finishing the first band's reductions: 0 none, 1 after the CG step
+    // (iteration count, relative residual, convergence test), 2 without it;
+    // fin_n per-block pairs (||r||^2, sum r) in fin_part
+    int fin, fin_n;
+    const double *fin_part;
     TailLevel<V> lev[kTailMaxLevels];
 };
 
 template <typename V>
 __global__ void __launch_bounds__(1024)
-k_msp_tail(const TailParams<V> P, const CgScalars *sc)
+k_msp_tail(const TailParams<V> P, CgScalars *sc)
 {
     if (halted(sc)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ int stop;
+    if (P.fin) {
+        // the first band's partials, summed in block order
+        double v[2] = {0.0, 0.0};
+        for (int b = threadIdx.x; b < P.fin_n; b += blockDim.x) {
+            v[0] += P.fin_part[2 * b];
+            v[1] += P.fin_part[2 * b + 1];
+        }
+        block_sum<2>(v);
+        if (threadIdx.x == 0) {
+            sc->rr = v[0];
+            sc->rs = v[1];
+            if (P.fin == 1) {
+                sc->iter += 1;
+                const double rel = sqrt(v[0]) / sc->bnorm;
+                sc->relres = rel;
+                if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
+                if (!isfinite(rel)) sc->flag = kBreakdown;
+                else if (rel <= sc->tol) sc->flag = kConverged;
+                else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+            }
+            stop = sc->flag != kRun;
+        }
+        __syncthreads();
+        if (stop) return;
+    }
     V *sa = reinterpret_cast<V *>(smem_raw + P.sa_s);
     V *sz = reinterpret_cast<V *>(smem_raw + P.sz_s);
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -628,7 +659,7 @@ k_msp_tail(const TailParams<V> P, const CgScalars *sc)
                 : "memory");
             if (done) break;
             if (clock64() - t0 > (1ll << 31)) {          // about a second: give up, flag it
-                if (tid == 0 && sc) const_cast<CgScalars *>(sc)->flag = kBreakdown;
+                if (tid == 0 && sc) sc->flag = kBreakdown;
                 return;
             }
         }

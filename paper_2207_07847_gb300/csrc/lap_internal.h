@@ -105,12 +105,13 @@ void expanded_edges(const HostModel &m, int which, std::vector<int64_t> &I,
 
 // Band sweeps (levels [k0, k1) of the sparsifier solve per launch): band
 // tops from level 0 up to kmax, and the tiles of one band (runs of level-k1
-// vertices whose descendants on levels k0..k1 fit `cap` bytes of shared
-// memory with values of sv bytes): tab holds ntiles + 1 rows of k1 - k0 + 1
-// first indices, fits one flag per tile (0: the tile runs in global memory).
+// vertices whose descendants on levels k0..k1 need at most `cap` bytes of
+// shared memory with values of sv bytes): tab holds ntiles + 1 rows of
+// k1 - k0 + 1 first indices, fits one flag per tile (0: the tile needs more
+// than cap_fit bytes and runs in global memory).
 constexpr int kBandMaxLevels = 16;
 std::vector<int> plan_band_tops(const HostModel &m, int kmax, int cap, int sv);
-void plan_band_tiles(const HostModel &m, int k0, int k1, int cap, int sv, std::vector<int> &tab,
+void plan_band_tiles(const HostModel &m, int k0, int k1, int cap, int cap_fit, int sv, std::vector<int> &tab,
                      std::vector<char> &fits, int &ntiles);
 
 // splitmix64 output i (>= 1) for `seed` (Steele, Lea & Flood 2014)

@@ -740,10 +740,11 @@ std::vector<int> plan_band_tops(const HostModel &m, int kmax, int cap, int sv)
     return tops;
 }
 
-// Tiles of band [k0, k1): runs of consecutive level-k1 vertices that fit
-// `cap` bytes (one vertex at least).  tab: ntiles + 1 rows of the L + 1 first
-// indices; fits: per tile, whether it fits (else it runs in global memory).
-void plan_band_tiles(const HostModel &m, int k0, int k1, int cap, int sv, std::vector<int> &tab,
+// Tiles of band [k0, k1): runs of consecutive level-k1 vertices needing at
+// most `cap` bytes (one vertex at least).  tab: ntiles + 1 rows of the L + 1
+// first indices; fits: per tile, whether it needs at most `cap_fit` bytes
+// (else it runs in global memory).
+void plan_band_tiles(const HostModel &m, int k0, int k1, int cap, int cap_fit, int sv, std::vector<int> &tab,
                      std::vector<char> &fits, int &ntiles)
 {
     const int L = k1 - k0;
@@ -759,7 +760,7 @@ void plan_band_tiles(const HostModel &m, int k0, int k1, int cap, int sv, std::v
     for (int64_t P0 = 0; P0 < N;) {
         int64_t P1 = P0 + 1;
         while (P1 < N && band_need(start, P0, P1 + 1, sv) <= cap) ++P1;
-        fits.push_back(band_need(start, P0, P1, sv) <= cap ? 1 : 0);
+        fits.push_back(band_need(start, P0, P1, sv) <= cap_fit ? 1 : 0);
         push(P1);
         ++ntiles;
         P0 = P1;

@@ -63,6 +63,7 @@ template <typename V> struct DevCsr {
     int *lrow_of = nullptr;            // per row: its index among the long rows
     int64_t ell_entries = 0, long_entries = 0;
     int kernel = 0;
+    int vec = 1;                       // SELL lane-group width (1, 2, 4)
 };
 
 template <typename V> struct DevMspLevel {

@@ -91,6 +91,7 @@ lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, Dev
     d.nslices = static_cast<int>(sl.nslices);
     d.nlong = static_cast<int>(sl.lrow.size());
     d.ell_entries = static_cast<int64_t>(sl.eci.size());
+    d.vec = sl.vec;
     d.long_entries = static_cast<int64_t>(sl.lci.size());
     if (share) {
         d.rp = share->rp;
@@ -461,9 +462,14 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
         }
         h.launches += 1;
         const int g = grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
-        k_sell<V, MODE><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.eci, A.ew, A.nlong,
-                                             A.lrow, A.lchunk_ptr, A.chunk_part, x, y, bs, yres, st.sc,
-                                             st.part, st.ticket);
+#define LAP_SELL(VEC)                                                                                   \
+    k_sell<V, MODE, VEC><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.eci, A.ew, A.nlong, A.lrow, \
+                                              A.lchunk_ptr, A.chunk_part, x, y, bs, yres, st.sc, st.part,   \
+                                              st.ticket)
+        if (A.vec == 4) LAP_SELL(4);
+        else if (A.vec == 2) LAP_SELL(2);
+        else LAP_SELL(1);
+#undef LAP_SELL
         return;
     }
     const int g = grid_for(h, static_cast<int64_t>(A.n) * tpr);

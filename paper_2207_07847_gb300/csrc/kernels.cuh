@@ -232,7 +232,65 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
     }
 }
 
-template <typename V, int MODE>
+// VEC consecutive entries of one lane (a lane group of the SELL layout) with
+// vector loads; the row sum is still accumulated entry by entry.
+template <typename V, int VEC> struct LaneGroup;
+template <typename V> struct LaneGroup<V, 1> {
+    __device__ __forceinline__ static V add(V s, V xi, const int *c, const V *w, const V *__restrict__ x)
+    {
+        return s + w[0] * (xi - x[c[0]]);
+    }
+};
+template <> struct LaneGroup<float, 2> {
+    __device__ __forceinline__ static float add(float s, float xi, const int *c, const float *w,
+                                                const float *__restrict__ x)
+    {
+        const int2 cc = __ldg(reinterpret_cast<const int2 *>(c));
+        const float2 ww = __ldg(reinterpret_cast<const float2 *>(w));
+        s += ww.x * (xi - x[cc.x]);
+        return s + ww.y * (xi - x[cc.y]);
+    }
+};
+template <> struct LaneGroup<float, 4> {
+    __device__ __forceinline__ static float add(float s, float xi, const int *c, const float *w,
+                                                const float *__restrict__ x)
+    {
+        const int4 cc = __ldg(reinterpret_cast<const int4 *>(c));
+        const float4 ww = __ldg(reinterpret_cast<const float4 *>(w));
+        s += ww.x * (xi - x[cc.x]);
+        s += ww.y * (xi - x[cc.y]);
+        s += ww.z * (xi - x[cc.z]);
+        return s + ww.w * (xi - x[cc.w]);
+    }
+};
+template <> struct LaneGroup<double, 2> {
+    __device__ __forceinline__ static double add(double s, double xi, const int *c, const double *w,
+                                                 const double *__restrict__ x)
+    {
+        const int2 cc = __ldg(reinterpret_cast<const int2 *>(c));
+        const double2 ww = __ldg(reinterpret_cast<const double2 *>(w));
+        s += ww.x * (xi - x[cc.x]);
+        return s + ww.y * (xi - x[cc.y]);
+    }
+};
+template <> struct LaneGroup<double, 4> {
+    __device__ __forceinline__ static double add(double s, double xi, const int *c, const double *w,
+                                                 const double *__restrict__ x)
+    {
+        const int4 cc = __ldg(reinterpret_cast<const int4 *>(c));
+        const double2 w0 = __ldg(reinterpret_cast<const double2 *>(w));
+        const double2 w1 = __ldg(reinterpret_cast<const double2 *>(w) + 1);
+        s += w0.x * (xi - x[cc.x]);
+        s += w0.y * (xi - x[cc.y]);
+        s += w1.x * (xi - x[cc.z]);
+        return s + w1.y * (xi - x[cc.w]);
+    }
+};
+
+// SELL-32 matvec in edge-difference form: one warp per slice of 32 rows,
+// lane l owning row 32 s + l and reading its entries VEC at a time (see
+// make_sell for the layout); long rows add their chunk partials.
+template <typename V, int MODE, int VEC>
 __global__ void __launch_bounds__(kBlock)
 k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__restrict__ lmask,
        const int *__restrict__ eci, const V *__restrict__ ew, int nlong, const int *__restrict__ lrow,
@@ -254,10 +312,11 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
             const int width = static_cast<int>((sptr[task + 1] - base) >> 5);
             const V xi = valid ? x[row] : V(0);
             V s = V(0);
-            const int *pc = eci + base + lane;
-            const V *pw = ew + base + lane;
-#pragma unroll 4
-            for (int j = 0; j < width; ++j) s += pw[32 * j] * (xi - x[pc[32 * j]]);
+            const int *pc = eci + base + lane * VEC;
+            const V *pw = ew + base + lane * VEC;
+            const int ng = width / VEC;
+#pragma unroll(VEC == 1 ? 4 : 2)
+            for (int g = 0; g < ng; ++g) s = LaneGroup<V, VEC>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
             if (valid && !((lmask[task] >> lane) & 1u)) spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
         } else if (lane == 0) {
             // long row: add its chunk partials in chunk order

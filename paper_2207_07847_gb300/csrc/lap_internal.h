@@ -54,6 +54,7 @@ struct HostCsr {                  // square CSR, off-diagonal entries + diagonal
 // listed as CSR rows processed by a whole warp each.
 struct HostSell {
     int64_t n = 0, nslices = 0;
+    int vec = 1;                      // entries per lane group (1, 2 or 4): see make_sell
     std::vector<int64_t> sptr;        // [nslices + 1]
     std::vector<uint32_t> longmask;   // [nslices] lanes whose row is a long row
     std::vector<int32_t> eci;
@@ -70,7 +71,13 @@ struct HostSell {
     std::vector<int64_t> chunk_beg;   // [nchunks + 1] entry ranges (into lci/lw)
 };
 
-void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold);
+// SELL-32 of A: slices of 32 rows, each padded to its longest row (rounded up
+// to a multiple of vec) and stored lane-interleaved in groups of vec entries:
+// entry j of lane l of slice s at sptr[s] + (j / vec) * 32 * vec + l * vec +
+// j % vec, so that a lane loads vec consecutive entries with one vector load.
+// Rows longer than long_threshold go to the long-row chunks.  vec = 0 picks
+// the largest of 4, 2, 1 whose padding adds at most 6% to the vec = 1 size.
+void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec = 0);
 
 struct HostMspLevel {             // elimination data of level k < l (tree order)
     int64_t n = 0, nagg = 0;

@@ -553,7 +553,7 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
 }
 
 // ---------------------------------------------------------------------------
-void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold)
+void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
 {
     const int64_t n = A.n;
     S.n = n;
@@ -564,8 +564,8 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold)
     S.lrp.assign(1, 0);
     S.lci.clear();
     S.lw.clear();
+    std::vector<int64_t> width(static_cast<size_t>(S.nslices), 0);
     for (int64_t s = 0; s < S.nslices; ++s) {
-        int64_t width = 0;
         for (int64_t lane = 0; lane < 32; ++lane) {
             const int64_t r = 32 * s + lane;
             if (r >= n) break;
@@ -579,10 +579,28 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold)
                 }
                 S.lrp.push_back(static_cast<int64_t>(S.lci.size()));
             } else {
-                width = std::max(width, d);
+                width[s] = std::max(width[s], d);
             }
         }
-        S.sptr[s + 1] = S.sptr[s] + 32 * width;
+    }
+    if (vec <= 0) {
+        auto size = [&](int v) {
+            int64_t t = 0;
+            for (int64_t w : width) t += 32 * ((w + v - 1) / v * v);
+            return t;
+        };
+        const int64_t base = size(1);
+        vec = 1;
+        for (int v : {4, 2})
+            if (size(v) * 100 <= base * 106) {
+                vec = v;
+                break;
+            }
+    }
+    S.vec = vec;
+    for (int64_t s = 0; s < S.nslices; ++s) {
+        const int64_t w = (width[s] + vec - 1) / vec * vec;
+        S.sptr[s + 1] = S.sptr[s] + 32 * w;
     }
     // chunks of the long rows
     const int64_t kChunk = 4096;
@@ -599,13 +617,13 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold)
     S.eci.assign(static_cast<size_t>(S.sptr[S.nslices]), 0);
     S.ew.assign(static_cast<size_t>(S.sptr[S.nslices]), 0.0);
     for (int64_t s = 0; s < S.nslices; ++s) {
-        const int64_t width = (S.sptr[s + 1] - S.sptr[s]) / 32;
+        const int64_t w = (S.sptr[s + 1] - S.sptr[s]) / 32;
         for (int64_t lane = 0; lane < 32; ++lane) {
             const int64_t r = 32 * s + lane;
             const bool real = r < n && !((S.longmask[s] >> lane) & 1u);
             const int64_t d = real ? A.rp[r + 1] - A.rp[r] : 0;
-            for (int64_t j = 0; j < width; ++j) {
-                const int64_t q = S.sptr[s] + 32 * j + lane;
+            for (int64_t j = 0; j < w; ++j) {
+                const int64_t q = S.sptr[s] + (j / vec) * 32 * vec + lane * vec + j % vec;
                 if (j < d) {
                     S.eci[q] = A.ci[A.rp[r] + j];
                     S.ew[q] = A.w[A.rp[r] + j];

@@ -183,26 +183,17 @@ __device__ __forceinline__ void band_coef_offsets(int L, BandTile &T)
     T.jw = jw;
 }
 
-// One level of the upward elimination for aggregates jl = first, first +
-// step, ... of the tile's level j (values in shared memory).
+// One level of the upward elimination of a staged tile, by threads
+// [tid0, tid0 + nthr).
 template <typename V>
 __device__ __forceinline__ void band_up_level(const BandParams<V> &P, const BandTile &T, unsigned char *sm, int j,
-                                              const V *F, int first, int step)
+                                              const V *F, int tid0, int nthr)
 {
-    const BandLevel<V> &Lv = P.lev[j];
     const int64_t onext = j + 1 < P.nlev ? P.lev[j + 1].off : P.off_top;
-    V *a = reinterpret_cast<V *>(sm + T.vs[j]);
-    V *an = reinterpret_cast<V *>(sm + T.vs[j + 1]);
-    const int *sg = reinterpret_cast<const int *>(sm + T.ss[j]);
-    const V *ci = reinterpret_cast<const V *>(sm + T.is[j]);
-    const V *cl = reinterpret_cast<const V *>(sm + T.ls[j]);
-    for (int jl = first; jl < T.cnt[j + 1]; jl += step) {
-        const int b = sg[jl], e = sg[jl + 1];
-        const V sum = agg_eliminate(a + b, a + b, e - b, cl + 3 * (b - 2 * jl), ci + 4 * jl);
-        V nx = Lv.gamma * sum;
-        if (F) nx += F[onext + T.st[j + 1] + jl];
-        an[jl] = nx;
-    }
+    elim_level(reinterpret_cast<V *>(sm + T.vs[j]), reinterpret_cast<V *>(sm + T.vs[j + 1]),
+               reinterpret_cast<const int *>(sm + T.ss[j]), 0, reinterpret_cast<const V *>(sm + T.is[j]),
+               reinterpret_cast<const V *>(sm + T.ls[j]), P.lev[j].gamma, F, onext + T.st[j + 1], T.cnt[j + 1],
+               tid0, nthr);
 }
 
 // Upward band: levels k0..k1-1 eliminated (deltas to the scratch, or in place
@@ -216,7 +207,7 @@ __device__ __forceinline__ void band_up_level(const BandParams<V> &P, const Band
 // F (optional): expanded right-hand side added on restriction (a_{k+1} +=
 // F_{k+1}; may alias A, read before it is overwritten).
 template <typename V, int MODE>
-__global__ void __launch_bounds__(kBandThreads)
+__global__ void __launch_bounds__(kBandThreads, 2)
 k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ p,
           const V *__restrict__ q, V *A, const V *F, CgScalars *sc, double *part, unsigned *ticket)
 {
@@ -305,7 +296,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
             __syncthreads();
             const int jw = T.jw;
             for (int j = 0; j < jw; ++j) {
-                band_up_level(P, T, band_raw, j, F, tid, kBandThreads);
+                band_up_level(P, T, band_raw, j, F, 0, kBandThreads);
                 __syncthreads();
             }
             // the small top levels by warp 0 while the other warps store the
@@ -313,7 +304,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
             V *ds = P.scratch + T.rec.ds / (long long)sizeof(V);
             if (tid < 32) {
                 for (int j = jw; j < L; ++j) {
-                    band_up_level(P, T, band_raw, j, F, tid, 32);
+                    band_up_level(P, T, band_raw, j, F, 0, 32);
                     __syncwarp();
                 }
             } else {
@@ -362,18 +353,10 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
             for (int j = 0; j < L; ++j) {
                 const BandLevel<V> &Lv = P.lev[j];
                 const int64_t onext = j + 1 < L ? P.lev[j + 1].off : P.off_top;
-                V *a = A + Lv.off + T.st[j];
-                V *an = A + onext + T.st[j + 1];
-                for (int jl = tid; jl < T.cnt[j + 1]; jl += kBandThreads) {
-                    const int J = T.st[j + 1] + jl;
-                    const int b = Lv.seg[J], e = Lv.seg[J + 1];
-                    V *m = a + (b - T.st[j]);
-                    const V sum = agg_eliminate(m, m, e - b, Lv.lcf + 3 * ((int64_t)b - 2 * (int64_t)J),
-                                                Lv.inv + 4 * (int64_t)J);
-                    V nx = Lv.gamma * sum;
-                    if (F) nx += F[onext + J];
-                    an[jl] = nx;
-                }
+                const int J0 = T.st[j + 1];
+                elim_level(A + Lv.off + T.st[j], A + onext + J0, Lv.seg + J0, T.st[j], Lv.inv + 4 * (int64_t)J0,
+                           Lv.lcf + 3 * ((int64_t)T.st[j] - 2 * (int64_t)J0), Lv.gamma, F, onext + J0,
+                           T.cnt[j + 1], 0, kBandThreads);
                 __syncthreads();
             }
         }
@@ -391,19 +374,15 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
     (void)ticket;
 }
 
-// One level of the downward pass for aggregates jl = first, first + step, ...
+// One level of the downward pass of a staged tile (in place), by threads
+// [tid0, tid0 + nthr).
 template <typename V>
 __device__ __forceinline__ void band_down_level(const BandParams<V> &P, const BandTile &T, unsigned char *sm, int j,
-                                                int first, int step)
+                                                int tid0, int nthr)
 {
-    const V dc = P.lev[j].dcoef;
-    const V *par = reinterpret_cast<const V *>(sm + T.vs[j + 1]);
     V *o = reinterpret_cast<V *>(sm + T.vs[j]);
-    const int *sg = reinterpret_cast<const int *>(sm + T.ss[j]);
-    for (int jl = first; jl < T.cnt[j + 1]; jl += step) {
-        const V base = P.pc * par[jl];
-        for (int u = sg[jl]; u < sg[jl + 1]; ++u) o[u] = base + dc * o[u];
-    }
+    prolong_level(o, o, reinterpret_cast<const V *>(sm + T.vs[j + 1]), reinterpret_cast<const int *>(sm + T.ss[j]),
+                  0, P.pc, P.lev[j].dcoef, T.cnt[j + 1], tid0, nthr);
 }
 
 // Downward band: for j = k1-1 .. k0, out_j(u) = pc * out_{j+1}(J) + dcoef_j *
@@ -415,7 +394,7 @@ __device__ __forceinline__ void band_down_level(const BandParams<V> &P, const Ba
 // CG; reduces sum z, r.z, z.q and finalises zmean, rho, beta.  A tile in
 // global memory reads its deltas in place from D (A for the sweeps).
 template <typename V, bool FINEST, bool DEXP>
-__global__ void __launch_bounds__(kBandThreads)
+__global__ void __launch_bounds__(kBandThreads, 2)
 k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V *out0, int write_all,
             int n, const V *__restrict__ r, const V *__restrict__ q, CgScalars *sc, double *part,
             unsigned *ticket)
@@ -496,12 +475,12 @@ k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V
             const int jw = T.jw;
             if (tid < 32)
                 for (int j = L - 1; j >= jw; --j) {
-                    band_down_level(P, T, band_raw, j, tid, 32);
+                    band_down_level(P, T, band_raw, j, 0, 32);
                     __syncwarp();
                 }
             __syncthreads();
             for (int j = jw - 1; j >= 0; --j) {
-                band_down_level(P, T, band_raw, j, tid, kBandThreads);
+                band_down_level(P, T, band_raw, j, 0, kBandThreads);
                 __syncthreads();
             }
             const V *z0 = reinterpret_cast<const V *>(band_raw + T.vs[0]);
@@ -548,13 +527,8 @@ k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V
                 const int64_t oup = j + 1 < L ? P.lev[j + 1].off : P.off_top;
                 const V *par = j + 1 < L ? Y + oup + T.st[j + 1] : Yp + P.off_top + T.st[L];
                 V *o = j == 0 ? out0 + T.st[0] : Y + Lv.off + T.st[j];
-                const V *d = D + Lv.off + T.st[j];
-                for (int jl = tid; jl < T.cnt[j + 1]; jl += kBandThreads) {
-                    const int J = T.st[j + 1] + jl;
-                    const V base = P.pc * par[jl];
-                    for (int u = Lv.seg[J] - T.st[j]; u < Lv.seg[J + 1] - T.st[j]; ++u)
-                        o[u] = base + Lv.dcoef * d[u];
-                }
+                prolong_level(o, D + Lv.off + T.st[j], par, Lv.seg + T.st[j + 1], T.st[j], P.pc, Lv.dcoef,
+                              T.cnt[j + 1], 0, kBandThreads);
                 __syncthreads();
             }
             if (FINEST)

@@ -221,7 +221,7 @@ kb_spmm(int n, int R, int CT, const int *__restrict__ rp, const int *__restrict_
             }
             if (MODE == 1 || MODE == 3) {
                 const double rv = Bs[k] - (double)s;
-                if (MODE == 1) yres[k] = rv;
+                if (MODE == 1 || yres) yres[k] = rv;
                 acc[0][j] += rv * rv;
                 acc[1][j] += rv;
             } else {
@@ -613,6 +613,35 @@ kb_scatter_range(int n, int R, int CT, int c0, int k, const int *__restrict__ pe
             const int c = cl + jj * CT;
             if (c >= c0 && c < c0 + k) X[(size_t)(c - c0) * n + dst] = (double)x[(size_t)i * R + c] - means[c];
         }
+    }
+}
+
+// Restart of stopped columns whose true residual missed the tolerance: r =
+// the true residual res (FP64, from kb_spmm) for columns c in [c0, c0 + k)
+// with flag converged and tres[c] > tol.  The flags are set afterwards by
+// kb_restart_flags (one block), so that every block decides alike here.
+template <typename V>
+__global__ void __launch_bounds__(kBThreads)
+kb_restart_copy(int n, int R, int CT, int c0, int k, const double *__restrict__ res, V *__restrict__ r,
+                const BCol *col, const double *__restrict__ tres, double tol)
+{
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S)
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            if (c < c0 || c >= c0 + k || col[c].flag != kConverged || !(tres[c] > tol)) continue;
+            r[(size_t)i * R + c] = (V)res[(size_t)i * R + c];
+        }
+}
+
+static __global__ void kb_restart_flags(int R, int c0, int k, BCol *col, const double *__restrict__ tres,
+                                        double tol)
+{
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        if (c < c0 || c >= c0 + k || col[c].flag != kConverged || !(tres[c] > tol)) continue;
+        col[c].flag = kRun;
+        col[c].first = 1;
+        col[c].join = 1;
     }
 }
 

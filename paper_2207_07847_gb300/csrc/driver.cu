@@ -1140,10 +1140,9 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
 
     const bool mixed = m.opt.precision == LAP_MIXED;
     const int64_t n = m.lev[0].n, nt = m.offset[m.levels];
-    const double avg = static_cast<double>(m.L1.rp[n]) / static_cast<double>(n);
     {
         HostSell sl;
-        make_sell(m.L1, sl, std::max<int64_t>(64, static_cast<int64_t>(8 * avg)));
+        make_sell(m.L1, sl, 0);
         LAP_TRY(upload_csr<double>(h, m.L1, sl, h.L64, nullptr));
         if (mixed) LAP_TRY(upload_csr<float>(h, m.L1, sl, h.L32, &h.L64));
     }
@@ -1151,8 +1150,7 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
     if (mixed) LAP_TRY(upload_msp<float>(h, m, h.M32, &h.M64));
     if (m.has_LH) {
         HostSell sl;
-        const double avgH = static_cast<double>(m.LH.rp[m.LH.n]) / static_cast<double>(m.LH.n);
-        make_sell(m.LH, sl, std::max<int64_t>(64, static_cast<int64_t>(8 * avgH)));
+        make_sell(m.LH, sl, 0);
         LAP_TRY(upload_csr<double>(h, m.LH, sl, h.H64, nullptr));
         if (mixed) LAP_TRY(upload_csr<float>(h, m.LH, sl, h.H32, &h.H64));
     }
@@ -1188,7 +1186,6 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
         h.L64.kernel = h.L32.kernel = autotune_spmv(h, h.L64, h.w64.p, h.w64.q);
         if (m.has_LH) h.H64.kernel = h.H32.kernel = autotune_spmv(h, h.H64, h.e64.p, h.e64.q);
     }
-    (void)avg;
     LAP_CK(cudaDeviceSynchronize());
     return LAP_OK;
 }

@@ -212,26 +212,6 @@ __device__ __forceinline__ void spmv_finish(int row, V xi, V s, V *y, const doub
     }
 }
 
-// Partial sums of the long rows, one warp per chunk of <= 4096 entries.
-template <typename V>
-__global__ void __launch_bounds__(kBlock)
-k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__restrict__ chunk_beg,
-              const int *__restrict__ lrow, const int *__restrict__ lci, const V *__restrict__ lw,
-              const V *__restrict__ x, V *__restrict__ chunk_part, const CgScalars *sc, int check)
-{
-    if (check && halted(sc)) return;
-    const int lane = threadIdx.x & 31;
-    const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nwarp) {
-        const V xi = x[lrow[chunk_row[c]]];
-        V s = V(0);
-        for (int64_t p = chunk_beg[c] + lane; p < chunk_beg[c + 1]; p += 32) s += lw[p] * (xi - x[lci[p]]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) chunk_part[c] = s;
-    }
-}
-
 // VEC consecutive entries of one lane (a lane group of the SELL layout) with
 // vector loads; the row sum is still accumulated entry by entry.
 template <typename V, int VEC> struct LaneGroup;
@@ -286,6 +266,30 @@ template <> struct LaneGroup<double, 4> {
         return s + w1.y * (xi - x[cc.w]);
     }
 };
+
+// Partial sums of the long rows, one warp per chunk of <= 4096 entries.
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__restrict__ chunk_beg,
+              const int *__restrict__ lrow, const int *__restrict__ lci, const V *__restrict__ lw,
+              const V *__restrict__ x, V *__restrict__ chunk_part, const CgScalars *sc, int check)
+{
+    if (check && halted(sc)) return;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nwarp) {
+        const V xi = x[lrow[chunk_row[c]]];
+        V s = V(0);
+        // chunks hold a multiple of 128 entries from a multiple-of-128 start:
+        // lane l takes entries 128 g + 4 l .. + 3 with one vector load each
+#pragma unroll 2
+        for (int64_t p = chunk_beg[c] + 4 * lane; p < chunk_beg[c + 1]; p += 128)
+            s = LaneGroup<V, 4>::add(s, xi, lci + p, lw + p, x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) chunk_part[c] = s;
+    }
+}
 
 // SELL-32 matvec in edge-difference form: one warp per slice of 32 rows,
 // lane l owning row 32 s + l and reading its entries VEC at a time (see
@@ -447,6 +451,112 @@ __device__ __forceinline__ V agg_eliminate(const V *a, V *d, int cnt, const V *l
     d[0] = da;
     d[1] = db;
     return sum;
+}
+
+// A warp eliminates one large aggregate: lanes take the leftovers in turn,
+// their sums are combined by a fixed shuffle tree, every lane solves the pair
+// and writes its leftovers.  Returns the sum of a (all lanes).
+template <typename V>
+__device__ __forceinline__ V warp_eliminate(V *a, int cnt, const V *lc, const V *cf, int lane)
+{
+    V s = V(0), ha = V(0), hb = V(0);
+    for (int t = 2 + lane; t < cnt; t += 32) {
+        const V al = a[t];
+        const V *c = lc + 3 * (t - 2);
+        s += al;
+        ha += c[0] * al;
+        hb += c[1] * al;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        ha += __shfl_xor_sync(0xffffffffu, ha, o);
+        hb += __shfl_xor_sync(0xffffffffu, hb, o);
+    }
+    const V aa = a[0], ab = a[1];
+    s += aa + ab;
+    ha += aa;
+    hb += ab;
+    V da, db;
+    pair_solve(cf, ha, hb, da, db);
+    for (int t = 2 + lane; t < cnt; t += 32) {
+        const V *c = lc + 3 * (t - 2);
+        a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        a[0] = da;
+        a[1] = db;
+    }
+    return s;
+}
+
+constexpr int kBigAgg = 32;   // aggregates with more members are eliminated by a warp
+
+// Upward elimination of one level of a tile, in place: aggregate jl (of na)
+// holds the members [sg[jl] - sbase, sg[jl + 1] - sbase) of a, its pair
+// coefficients at ci + 4 jl and the leftover coefficients of member b + t at
+// cl + 3 (b - 2 jl) + 3 (t - 2); an[jl] = gamma * (sum of its members) +
+// F[fofs + jl] (if F).  Threads [tid0, tid0 + nthr) take part, whole warps;
+// aggregates of more than kBigAgg members go to a warp each.
+template <typename V>
+__device__ __forceinline__ void elim_level(V *a, V *an, const int *sg, int sbase, const V *ci, const V *cl, V gamma,
+                                           const V *F, int64_t fofs, int na, int tid0, int nthr)
+{
+    const int t = threadIdx.x - tid0;
+    for (int jl = t; jl < na; jl += nthr) {
+        const int b = sg[jl] - sbase, e = sg[jl + 1] - sbase;
+        if (e - b > kBigAgg) continue;
+        const V sum = agg_eliminate(a + b, a + b, e - b, cl + 3 * (b - 2 * jl), ci + 4 * jl);
+        V nx = gamma * sum;
+        if (F) nx += F[fofs + jl];
+        an[jl] = nx;
+    }
+    const int lane = t & 31, nw = nthr >> 5;
+    for (int q = t >> 5; q * 32 < na; q += nw) {
+        const int j0 = q * 32 + lane;
+        const bool big = j0 < na && sg[j0 + 1] - sg[j0] > kBigAgg;
+        unsigned m = __ballot_sync(0xffffffffu, big);
+        while (m) {
+            const int jl = q * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            const int b = sg[jl] - sbase, e = sg[jl + 1] - sbase;
+            const V sum = warp_eliminate(a + b, e - b, cl + 3 * (b - 2 * jl), ci + 4 * jl, lane);
+            if (lane == 0) {
+                V nx = gamma * sum;
+                if (F) nx += F[fofs + jl];
+                an[jl] = nx;
+            }
+        }
+    }
+}
+
+// Downward pass of one level of a tile: o[u] = pc * par[jl] + dc * d[u] for
+// the members u of aggregate jl (o may alias d); large aggregates by a warp.
+template <typename V>
+__device__ __forceinline__ void prolong_level(V *o, const V *d, const V *par, const int *sg, int sbase, V pc, V dc,
+                                              int na, int tid0, int nthr)
+{
+    const int t = threadIdx.x - tid0;
+    for (int jl = t; jl < na; jl += nthr) {
+        const int b = sg[jl] - sbase, e = sg[jl + 1] - sbase;
+        if (e - b > kBigAgg) continue;
+        const V base = pc * par[jl];
+        for (int u = b; u < e; ++u) o[u] = base + dc * d[u];
+    }
+    const int lane = t & 31, nw = nthr >> 5;
+    for (int q = t >> 5; q * 32 < na; q += nw) {
+        const int j0 = q * 32 + lane;
+        const bool big = j0 < na && sg[j0 + 1] - sg[j0] > kBigAgg;
+        unsigned m = __ballot_sync(0xffffffffu, big);
+        while (m) {
+            const int jl = q * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            const int b = sg[jl] - sbase, e = sg[jl + 1] - sbase;
+            const V base = pc * par[jl];
+            for (int u = b + lane; u < e; u += 32) o[u] = base + dc * d[u];
+        }
+    }
 }
 
 // Upward pass over one level, tiled.
@@ -725,35 +835,10 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
     }
     for (int k = 0; k < P.nlev; ++k) {
         const TailLevel<V> &L = P.lev[k];
-        V *a = sa + L.loc;
-        const int *seg = reinterpret_cast<const int *>(smem_raw + L.seg_s);
-        const V *inv = reinterpret_cast<const V *>(smem_raw + L.inv_s);
-        const V *lcf = reinterpret_cast<const V *>(smem_raw + L.lcf_s);
         const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
-        for (int J = tid; J < L.nagg; J += nth) {
-            const int b0 = seg[J], e = seg[J + 1];
-            const V aa = a[b0], ab = a[b0 + 1];
-            V sum = aa + ab, ha = aa, hb = ab;
-            const V *lc = lcf + 3 * (b0 - 2 * J);
-            for (int t = b0 + 2; t < e; ++t) {
-                const V al = a[t];
-                const V *c = lc + 3 * (t - b0 - 2);
-                sum += al;
-                ha += c[0] * al;
-                hb += c[1] * al;
-            }
-            V da, db;
-            pair_solve(inv + 4 * J, ha, hb, da, db);
-            for (int t = b0 + 2; t < e; ++t) {
-                const V *c = lc + 3 * (t - b0 - 2);
-                a[t] = a[t] * c[2] + c[0] * da + c[1] * db;
-            }
-            a[b0] = da;
-            a[b0 + 1] = db;
-            V nx = L.gamma * sum;
-            if (P.F) nx += P.F[P.off0 + nloc + J];
-            sa[nloc + J] = nx;
-        }
+        elim_level(sa + L.loc, sa + nloc, reinterpret_cast<const int *>(smem_raw + L.seg_s), 0,
+                   reinterpret_cast<const V *>(smem_raw + L.inv_s), reinterpret_cast<const V *>(smem_raw + L.lcf_s),
+                   L.gamma, P.F, P.off0 + nloc, L.nagg, 0, nth);
         __syncthreads();
     }
     {   // top: dense pseudo-inverse, one warp per row
@@ -770,12 +855,9 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
     __syncthreads();
     for (int k = P.nlev - 1; k >= 0; --k) {
         const TailLevel<V> &L = P.lev[k];
-        const int *seg = reinterpret_cast<const int *>(smem_raw + L.seg_s);
         const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
-        for (int J = tid; J < L.nagg; J += nth) {
-            const V base = P.pc * sz[nloc + J];
-            for (int u = seg[J]; u < seg[J + 1]; ++u) sz[L.loc + u] = base + L.dcoef * sa[L.loc + u];
-        }
+        prolong_level(sz + L.loc, sa + L.loc, sz + nloc, reinterpret_cast<const int *>(smem_raw + L.seg_s), 0, P.pc,
+                      L.dcoef, L.nagg, 0, nth);
         __syncthreads();
     }
     const int nout = P.write_all ? P.ntail : P.n0;

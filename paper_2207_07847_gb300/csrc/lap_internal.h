@@ -75,7 +75,8 @@ struct HostSell {
 // to a multiple of vec) and stored lane-interleaved in groups of vec entries:
 // entry j of lane l of slice s at sptr[s] + (j / vec) * 32 * vec + l * vec +
 // j % vec, so that a lane loads vec consecutive entries with one vector load.
-// Rows longer than long_threshold go to the long-row chunks.  vec = 0 picks
+// Rows longer than long_threshold go to the long-row chunks (threshold 0:
+// chosen from the row lengths, see choose_long_threshold).  vec = 0 picks
 // the largest of 4, 2, 1 whose padding adds at most 6% to the vec = 1 size.
 void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec = 0);
 

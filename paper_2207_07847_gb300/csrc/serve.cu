@@ -46,6 +46,7 @@ struct Request {
     bool cancel = false;
     bool started = false;
     int c0 = -1;
+    int restarts = 0;                // true-residual restarts so far
     int64_t launches0 = 0;           // batch launch counter at admission
     lap_solve_info info{};
 };
@@ -59,6 +60,7 @@ struct GraphBatch {
     std::vector<BCol> cols;
     int64_t launches = 0;            // kernels launched for this batch
     bool launched = false;
+    bool rejoin = false;             // restarted columns wait for their first direction
     ~GraphBatch()
     {
         if (s) cudaStreamSynchronize(s);
@@ -67,6 +69,8 @@ struct GraphBatch {
         if (s) cudaStreamDestroy(s);
     }
 };
+
+constexpr int kServeRestarts = 4;     // true-residual restarts per request
 
 int batch_width(const lap_server_options &o) { return std::min(256, pow2_at_least(o.max_slots)); }
 
@@ -232,10 +236,11 @@ lap_status launch(lap_server_s &S, GraphBatch &gb)
         r->started = true;
         joined = true;
     }
-    if (joined) {
+    if (joined || gb.rejoin) {
         // z = B r for every column: the running columns recompute the z, rho
         // they already hold (same operands, same order: the same bits), and
-        // only the joining columns take their first direction from it
+        // only the joining (or restarted) columns take their first direction
+        gb.rejoin = false;
         bprecond<double>(h, b, v, false, gb.s);
         kb_pupdate_join<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
             n, R, CT, o.prec == LAP_PREC_NONE ? v.r : v.z, v.p, v.col);
@@ -301,8 +306,35 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
         if (stopped) done.push_back({r, forced});
     }
     if (done.empty()) return LAP_OK;
-    // true residuals of all columns (column states untouched), means, results
-    bspmm<double, 3>(h, b, h.L64, v.x, nullptr, nullptr, v.chunk, v.col, gb.s);
+    // true residuals of all columns (column states untouched) to r64 and tres
+    bspmm<double, 3>(h, b, h.L64, v.x, nullptr, b.r64, v.chunk, v.col, gb.s);
+    std::vector<double> tres(static_cast<size_t>(R));
+    LAP_BCK(cudaMemcpyAsync(tres.data(), b.tres, sizeof(double) * R, cudaMemcpyDeviceToHost, gb.s));
+    LAP_BCK(cudaStreamSynchronize(gb.s));
+    // a request whose recurrence converged but whose true residual missed the
+    // tolerance restarts those columns from their true residual (x kept)
+    const double tol = h.m.opt.tol;
+    std::vector<Done> fin;
+    for (const Done &d : done) {
+        bool miss = false;
+        for (int j = d.r->c0; j < d.r->c0 + d.r->nrhs; ++j)
+            miss |= gb.cols[j].flag == kConverged && !(tres[j] <= tol);
+        if (d.forced == LAP_OK && miss && d.r->restarts < kServeRestarts) {
+            d.r->restarts += 1;
+            kb_restart_copy<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
+                n, R, CT, d.r->c0, d.r->nrhs, b.r64, v.r, v.col, b.tres, tol);
+            kb_restart_flags<<<1, 256, 0, gb.s>>>(R, d.r->c0, d.r->nrhs, v.col, b.tres, tol);
+            h.launches += 2;
+            gb.rejoin = true;
+        } else {
+            fin.push_back(d);
+        }
+    }
+    done.swap(fin);
+    if (done.empty()) {
+        gb.launches += h.launches - l0;
+        return LAP_OK;
+    }
     kb_mean<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(n, R, CT, v.x, b.means, b.part, b.ticket);
     h.launches += 1;
     for (const Done &d : done) {
@@ -310,8 +342,6 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
             n, R, CT, d.r->c0, d.r->nrhs, h.perm1, v.x, b.means, d.r->X);
         h.launches += 1;
     }
-    std::vector<double> tres(static_cast<size_t>(R));
-    LAP_BCK(cudaMemcpyAsync(tres.data(), b.tres, sizeof(double) * R, cudaMemcpyDeviceToHost, gb.s));
     LAP_BCK(cudaStreamSynchronize(gb.s));
     gb.launches += h.launches - l0;
     for (const Done &d : done) {
@@ -329,6 +359,7 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
         if (st == LAP_OK && !(rel <= h.m.opt.tol)) st = LAP_ERR_NO_CONVERGENCE;
         if (d.forced != LAP_OK) st = d.forced;
         r->info.iterations = it;
+        r->info.restarts = r->restarts;
         r->info.relres = rel;
         r->info.relres_recurrence = 0.0;
         for (int j = r->c0; j < r->c0 + r->nrhs; ++j)

@@ -553,9 +553,45 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
 }
 
 // ---------------------------------------------------------------------------
+// Long-row threshold of the SELL layout.  The default is eight times the mean
+// row length (at least 64); another candidate is taken only if it stores at
+// least a fifth fewer entries, counting each slice padded to its longest
+// short row and each long row padded to whole 128-entry groups plus one group
+// of overhead (power-law rows: hubs otherwise pad whole slices).
+static int64_t choose_long_threshold(const HostCsr &A)
+{
+    const int64_t n = A.n, ns = (n + 31) / 32;
+    auto cost = [&](int64_t T) {
+        int64_t c = 0;
+        for (int64_t s = 0; s < ns; ++s) {
+            int64_t w = 0;
+            for (int64_t r = 32 * s; r < std::min(n, 32 * s + 32); ++r) {
+                const int64_t d = A.rp[r + 1] - A.rp[r];
+                if (d > T) c += (d + 127) / 128 * 128 + 128;
+                else w = std::max(w, d);
+            }
+            c += 32 * w;
+        }
+        return c;
+    };
+    const double avg = n > 0 ? static_cast<double>(A.rp[n]) / static_cast<double>(n) : 0.0;
+    const int64_t t0 = std::max<int64_t>(64, static_cast<int64_t>(8 * avg));
+    const int64_t c0 = cost(t0);
+    int64_t best = t0, best_cost = c0;
+    for (int64_t T : {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 2048, 4096}) {
+        const int64_t c = cost(T);
+        if (c < best_cost) {
+            best_cost = c;
+            best = T;
+        }
+    }
+    return best_cost * 5 < c0 * 4 ? best : t0;
+}
+
 void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
 {
     const int64_t n = A.n;
+    if (long_threshold <= 0) long_threshold = choose_long_threshold(A);
     S.n = n;
     S.nslices = (n + 31) / 32;
     S.sptr.assign(static_cast<size_t>(S.nslices) + 1, 0);
@@ -602,17 +638,36 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
         const int64_t w = (width[s] + vec - 1) / vec * vec;
         S.sptr[s + 1] = S.sptr[s] + 32 * w;
     }
-    // chunks of the long rows
+    // chunks of the long rows: at most kChunk entries each, padded (column =
+    // the row itself, weight 0) to a multiple of 128 entries, so that a warp
+    // reads a chunk as groups of 4 consecutive entries per lane; lrp becomes
+    // the padded range of each long row
     const int64_t kChunk = 4096;
     S.lchunk_ptr.assign(1, 0);
     S.chunk_row.clear();
     S.chunk_beg.assign(1, 0);
-    for (size_t r = 0; r < S.lrow.size(); ++r) {
-        for (int64_t b = S.lrp[r]; b < S.lrp[r + 1]; b += kChunk) {
-            S.chunk_row.push_back(static_cast<int32_t>(r));
-            S.chunk_beg.push_back(std::min(b + kChunk, S.lrp[r + 1]));
+    {
+        std::vector<int32_t> ci;
+        std::vector<double> w;
+        std::vector<int64_t> rp(1, 0);
+        for (size_t r = 0; r < S.lrow.size(); ++r) {
+            for (int64_t b = S.lrp[r]; b < S.lrp[r + 1]; b += kChunk) {
+                const int64_t e = std::min(b + kChunk, S.lrp[r + 1]);
+                ci.insert(ci.end(), S.lci.begin() + b, S.lci.begin() + e);
+                w.insert(w.end(), S.lw.begin() + b, S.lw.begin() + e);
+                while (ci.size() % 128) {
+                    ci.push_back(S.lrow[r]);
+                    w.push_back(0.0);
+                }
+                S.chunk_row.push_back(static_cast<int32_t>(r));
+                S.chunk_beg.push_back(static_cast<int64_t>(ci.size()));
+            }
+            S.lchunk_ptr.push_back(static_cast<int32_t>(S.chunk_row.size()));
+            rp.push_back(static_cast<int64_t>(ci.size()));
         }
-        S.lchunk_ptr.push_back(static_cast<int32_t>(S.chunk_row.size()));
+        S.lci.swap(ci);
+        S.lw.swap(w);
+        S.lrp.swap(rp);
     }
     S.eci.assign(static_cast<size_t>(S.sptr[S.nslices]), 0);
     S.ew.assign(static_cast<size_t>(S.sptr[S.nslices]), 0.0);

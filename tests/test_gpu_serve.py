@@ -225,3 +225,27 @@ def test_latency_under_load(graphs):
         assert lat[0] > 0 and np.isfinite(lat).all()
     finally:
         S.close()
+
+
+def test_true_residual_restart():
+    """A tolerance near what FP64 CG can reach on an ill-conditioned grid: a
+    column whose recurrence converged while its true residual did not is
+    restarted from the true residual, so that a request reported converged
+    really is, and the restart count is reported."""
+    g = gg.grid3d(20, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    h = P.lap_setup(g, seed=5, maxit=20000, tol=3e-13)
+    S = P.Server(max_slots=8)
+    try:
+        B = _cols(g.n, 4, seed=21)
+        Bd = torch.as_tensor(B, device="cuda")
+        Xd = torch.empty_like(Bd)
+        st, info = S.wait(S.submit(h, Bd, Xd), 120.0)
+        assert st in (0, 7), info.as_dict()
+        X = Xd.cpu().numpy()
+        worst = max(_relres(g, B[j], X[j]) for j in range(4))
+        assert abs(worst - info.relres) <= 1e-3 * worst + 1e-16
+        if st == 0:
+            assert worst <= 3e-13
+        assert 0 <= info.restarts <= 4
+    finally:
+        S.close()

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--nx", type=int, default=WORKLOAD["nx"], help="grid side (128 = the workload)")
     ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["pegp_inner", "msp", "none"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--powerlaw-n", type=int, default=1 << 20,
+                    help="vertices of the Chung-Lu line (0: skip it)")
     ap.add_argument("--batched-scale", type=int, default=20,
                     help="R-MAT scale of the batched line (0: skip it)")
     ap.add_argument("--batched-rhs", type=int, default=256)
@@ -356,6 +358,8 @@ def bench_ours(args, rank, world):
         "failed_solves": failed,
     }
     h.close()
+    if args.powerlaw_n > 0:
+        result["powerlaw"] = bench_powerlaw(args, dev, world)
     if args.batched_scale > 0:
         result["batched"] = bench_batched(args, dev, world)
     if args.serve_requests > 0:
@@ -371,6 +375,45 @@ def bench_ours(args, rank, world):
 def _pct(v, q):
     v = sorted(v)
     return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+
+def bench_powerlaw(args, dev, world):
+    """Chung-Lu power-law graph (2^20 vertices, mean degree 16, exponent 2.5,
+    largest component, weights uniform in (0, 1]): PCG with the MSP, mixed
+    precision against plain FP64, one N(0,1) right-hand side per solve."""
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+    t0 = time.perf_counter()
+    g = gg.chung_lu(args.powerlaw_n, avg_deg=16.0, gamma=2.5, weights="uniform01", seed=4)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h = P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                    tol=WORKLOAD["tol"], maxit=20000)
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    out = {"workload": f"chunglu_{args.powerlaw_n}_d16_g2.5_uniform01_MSP_mu0.8", "n": g.n,
+           "nnz": P.lap_get_hierarchy_info(h)["nnz"], "gen_s": round(gen_s, 2), "setup_s": round(setup_s, 2)}
+    for precision in ("mixed", "fp64"):
+        P.lap_update_options(h, precision=precision)
+        bs = [torch.as_tensor(gg.rhs(g.n, seed=800 + i), device=dev) for i in range(4)]
+        P.lap_pcg_solve(h, bs[0], x)                                 # warm-up
+        ranks_barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [P.lap_pcg_solve(h, b, x) for b in bs[1:]]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        out[precision] = {"value": whole_job_rate(len(infos), world, ms), "unit": "solves/s",
+                          "iterations": [i.iterations for i in infos],
+                          "relres_max": max(i.relres for i in infos),
+                          "failed": sum(1 for i in infos if i.status != 0)}
+    h.close()
+    return out
 
 
 def bench_batched(args, dev, world):
@@ -452,8 +495,9 @@ def bench_serving(args, dev, world):
     mean degree 8..32, random geometric graphs; weights log-uniform in
     [1e-2, 1e2]), `serve_requests` requests of 1..16 N(0,1) right-hand sides
     arriving as a Poisson stream at half the server's measured capacity
-    (MSP, mu = 0.8, relres 1e-8).  The same stream (a prefix of it, within
-    a time limit) through the plain FP64 single-solve path for comparison."""
+    (MSP, mu = 0.8, relres 1e-8; FP32 columns refined per request in FP64).
+    The same stream (a prefix of it, within a time limit) through the plain
+    FP64 single-solve path for comparison."""
     import numpy as np
     import torch
 
@@ -466,7 +510,7 @@ def bench_serving(args, dev, world):
     graphs = [_serving_graph(kinds[i % 4], sizes[i], rng, 300 + i) for i in range(G)]
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hs = [P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="fp64", seed=WORKLOAD["setup_seed"],
+    hs = [P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
                       tol=WORKLOAD["tol"], maxit=20000) for g in graphs]
     setup_s = time.perf_counter() - t0
     R = args.serve_requests
@@ -515,6 +559,8 @@ def bench_serving(args, dev, world):
     rhs_total = int(nr.sum())
     wall = max_over_ranks(wall, world, dev)
     # plain FP64 single solves of the same stream (prefix), FIFO, real time
+    for h in hs:
+        P.lap_update_options(h, precision="fp64")
     plain_lat, plain_rhs = [], 0
     x1 = {}
     start = time.perf_counter()
@@ -539,7 +585,8 @@ def bench_serving(args, dev, world):
             "graphs": {"count": G, "n_min": int(min(g.n for g in graphs)),
                        "n_max": int(max(g.n for g in graphs)), "kinds": kinds},
             "requests": R, "rhs_total": rhs_total, "arrival_rate_req_s": round(lam, 2),
-            "precision": "fp64 columns, 16 per graph batch", "value": whole_job_rate(rhs_total, world, wall * 1e3),
+            "precision": "mixed (FP32 columns refined per request in FP64), 16 per graph batch",
+            "value": whole_job_rate(rhs_total, world, wall * 1e3),
             "unit": "solves/s", "requests_per_s": R * world / wall,
             "latency_ms": {"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99)}, "failed": failed,
             "failed_info": failed_info, "restarted_requests": restarted,

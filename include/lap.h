@@ -335,8 +335,14 @@ lap_status lap_laplacian_residual_noalloc(int64_t n, const int64_t *d_row_ptr,
  *     iteration limit, breakdown, cancelled, timed out) gets its solution
  *     (mean-zero, caller's vertex numbering) written to its d_X, its info
  *     filled and its callback called; its columns become free at once.
- * Columns run in FP64 whatever the handle's precision option; tol, maxit and
- * timeout_s come from the handle's options.  Every column's arithmetic is
+ * On a LAP_FP64 handle the columns run in FP64, and a column whose recurrence
+ * converged while its true residual did not restarts from the true residual
+ * (at most 4 times).  On a LAP_MIXED handle the columns run the FP32 CG and
+ * each request is refined against its FP64 true residual (refine_tol,
+ * max_refine as for lap_pcg_solve): when its inner solves have stopped, the
+ * corrections go into its FP64 solution and the columns still above the
+ * tolerance start the next inner solve.  tol, maxit and timeout_s come from
+ * the handle's options.  Every column's arithmetic is
  * independent of the other columns and of the moment it joined, so a
  * request's result is bitwise the same whether it ran alone or with others
  * on the same server (same handle, same max_slots).

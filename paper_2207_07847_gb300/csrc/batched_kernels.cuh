@@ -534,11 +534,13 @@ kb_join_gather(int n, int R, int CT, int c0, int k, const int *__restrict__ perm
             if (c >= c0 && c < c0 + k) col[c].bmean = tot[c] / (double)n;
 }
 
-// Centre the joining columns, r = Bs, x = 0 there, and start their CG.
+// Centre the joining columns, r = Bs, x = 0 there (and x64 = 0 if given:
+// the FP64 solution of a refined column), and start their CG.
 template <typename V>
 __global__ void __launch_bounds__(kBThreads)
 kb_join_center(int n, int R, int CT, int c0, int k, double *__restrict__ Bs, V *__restrict__ r,
-               V *__restrict__ x, BCol *col, double tol, int maxit, double *part, unsigned *ticket)
+               V *__restrict__ x, BCol *col, double tol, int maxit, double *part, unsigned *ticket,
+               double *__restrict__ x64)
 {
     __shared__ double tot[512];
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
@@ -553,6 +555,7 @@ kb_join_center(int n, int R, int CT, int c0, int k, double *__restrict__ Bs, V *
             Bs[q] = v;
             r[q] = (V)v;
             x[q] = V(0);
+            if (x64) x64[q] = 0.0;
             acc[0][j] += v * v;
             acc[1][j] += v;
         }
@@ -642,6 +645,61 @@ static __global__ void kb_restart_flags(int R, int c0, int k, BCol *col, const d
         col[c].flag = kRun;
         col[c].first = 1;
         col[c].join = 1;
+    }
+}
+
+// Mixed-precision refinement of served columns.  x64(:, c) += x(:, c), then
+// x(:, c) = 0, for the columns c in [c0, c0 + k) (their inner solves ended).
+template <typename V>
+__global__ void __launch_bounds__(kBThreads)
+kb_add_cols(int n, int R, int CT, int c0, int k, double *__restrict__ x64, V *__restrict__ x)
+{
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S)
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            if (c >= c0 && c < c0 + k) {
+                const size_t q = (size_t)i * R + c;
+                x64[q] += (double)x[q];
+                x[q] = V(0);                    // added once: a column not refined again adds nothing
+            }
+        }
+}
+
+// Next inner solve of the columns in range whose true residual tres[c] is
+// above tol: r = (V) res (the FP64 true residual), x = 0.
+template <typename V>
+__global__ void __launch_bounds__(kBThreads)
+kb_refine_copy(int n, int R, int CT, int c0, int k, const double *__restrict__ res, V *__restrict__ r,
+               V *__restrict__ x, const double *__restrict__ tres, double tol)
+{
+    const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S)
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            if (c < c0 || c >= c0 + k || !(tres[c] > tol)) continue;
+            const size_t q = (size_t)i * R + c;
+            r[q] = (V)res[q];
+            x[q] = V(0);
+        }
+}
+
+// ...and their CG state: running again from a first direction, tolerance
+// max(refine_tol, 0.3 tol / tres) relative to ||Pi b|| times tres (the inner
+// system's right-hand side is the residual), at most 0.5; maxit per solve.
+static __global__ void kb_refine_flags(int R, int c0, int k, BCol *col, const double *__restrict__ tres, double tol,
+                                       double refine_tol, int maxit)
+{
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        if (c < c0 || c >= c0 + k || !(tres[c] > tol)) continue;
+        BCol &C = col[c];
+        const double rel = fmin(0.5, fmax(refine_tol, 0.3 * tol / tres[c]));
+        C.flag = kRun;
+        C.first = 1;
+        C.join = 1;
+        C.iter = 0;
+        C.maxit = maxit;
+        C.tol = rel * tres[c];                 // relative to ||Pi b|| (the column's bnorm)
     }
 }
 

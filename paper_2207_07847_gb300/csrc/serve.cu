@@ -13,7 +13,12 @@
 //   3. reads the column flags, retires every request whose columns have all
 //      stopped (true residuals, projection, results written back, callback),
 //      and frees a batch once it is empty.
-// Columns run FP64 here whatever the handle's precision.
+// On a LAP_MIXED handle the columns run the FP32 CG and each request is
+// refined against its own FP64 true residual: when a request's inner solves
+// have stopped, their corrections are added to its FP64 solution and the
+// columns whose true residual misses the tolerance start the next inner solve
+// from it.  On a LAP_FP64 handle the columns run in FP64 and restart from the
+// true residual if their recurrence converged but the true residual did not.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -22,6 +27,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 #include <unordered_map>
 
 #include "batched_impl.cuh"
@@ -46,7 +52,8 @@ struct Request {
     bool cancel = false;
     bool started = false;
     int c0 = -1;
-    int restarts = 0;                // true-residual restarts so far
+    int restarts = 0;                // true-residual restarts (FP64) or refinements (mixed)
+    int iters = 0;                   // iterations of the finished inner solves (mixed)
     int64_t launches0 = 0;           // batch launch counter at admission
     lap_solve_info info{};
 };
@@ -61,6 +68,7 @@ struct GraphBatch {
     int64_t launches = 0;            // kernels launched for this batch
     bool launched = false;
     bool rejoin = false;             // restarted columns wait for their first direction
+    bool mixed = false;              // FP32 columns refined in FP64
     ~GraphBatch()
     {
         if (s) cudaStreamSynchronize(s);
@@ -79,11 +87,15 @@ int iterations_per_launch(const lap_server_options &o, const lap_handle_s &h)
     return o.check_every > 0 ? o.check_every : h.m.opt.check_every;
 }
 
-// Upper estimate of make_batch's FP64 allocations for R columns.
+bool serve_mixed(const lap_handle_s &h) { return h.m.opt.precision == LAP_MIXED && h.L32.w != nullptr; }
+
+// Upper estimate of make_batch's allocations for R columns (FP64 vectors, and
+// FP32 ones for a mixed handle).
 int64_t batch_bytes_estimate(const lap_handle_s &h, int R)
 {
     const int64_t n = h.m.lev[0].n, nt = h.m.offset[h.m.levels];
-    const int64_t words = R * (8 * n + 2 * nt + std::max(h.L64.nchunks, 1)) + 2 * int64_t(kMaxRedBlocks) * R;
+    int64_t words = R * (8 * n + 2 * nt + std::max(h.L64.nchunks, 1)) + 2 * int64_t(kMaxRedBlocks) * R;
+    if (serve_mixed(h)) words += R * (5 * n + 2 * nt + std::max(h.L32.nchunks, 1)) / 2;
     return 8 * words + (int64_t(1) << 20);
 }
 
@@ -132,11 +144,12 @@ lap_status create_batch(lap_server_s &S, lap_handle_s *h, GraphBatch *&out)
     gb->h = h;
     LAP_BCK(cudaStreamCreateWithFlags(&gb->s, cudaStreamNonBlocking));
     LAP_BCK(cudaEventCreateWithFlags(&gb->ev, cudaEventDisableTiming));
-    LAP_LTRY(make_batch(*h, S.R, false, gb->s, gb->w));
+    gb->mixed = serve_mixed(*h);
+    LAP_LTRY(make_batch(*h, S.R, gb->mixed, gb->s, gb->w));
     gb->owner.assign(static_cast<size_t>(S.R), nullptr);
     gb->cols.assign(static_cast<size_t>(S.R), BCol{});
     // every column starts stopped; a request's columns are started on join
-    kb_set_flags<<<1, 256, 0, gb->s>>>(S.R, 0, S.R, gb->w->v64.col, kConverged);
+    kb_set_flags<<<1, 256, 0, gb->s>>>(S.R, 0, S.R, gb->mixed ? gb->w->v32.col : gb->w->v64.col, kConverged);
     LAP_BCK(cudaGetLastError());
     gb->launches += 1;
     S.used_bytes += gb->w->bytes;
@@ -216,22 +229,28 @@ void admit(lap_server_s &S)
 
 // Start the newly admitted columns of gb, then launch one chunk of
 // iterations and the copy of the column states.
-lap_status launch(lap_server_s &S, GraphBatch &gb)
+template <typename V>
+lap_status launch_t(lap_server_s &S, GraphBatch &gb)
 {
     lap_handle_s &h = *gb.h;
     BatchWork &b = *gb.w;
-    auto &v = b.v64;
+    auto &v = vecs<V>(b);
+    const bool mixed = std::is_same<V, float>::value;
     const int n = static_cast<int>(b.n), R = b.R, CT = b.CT;
     const lap_options &o = h.m.opt;
     const int64_t l0 = h.launches;
+    // the first inner solve of a refined column: relative tolerance
+    // max(refine_tol, 0.3 tol), at most 0.5
+    const double tol0 = mixed ? std::min(0.5, std::max(o.refine_tol, 0.3 * o.tol)) : o.tol;
     bool joined = false;
     for (int c = 0; c < R; ++c) {
         Request *r = gb.owner[c];
         if (!r || r->started || c != r->c0) continue;
         kb_join_gather<<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(n, R, CT, r->c0, r->nrhs, h.perm1, r->B,
                                                                    b.Bs, v.col, b.part, b.ticket);
-        kb_join_center<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
-            n, R, CT, r->c0, r->nrhs, b.Bs, v.r, v.x, v.col, o.tol, o.maxit, b.part, b.ticket);
+        kb_join_center<V><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
+            n, R, CT, r->c0, r->nrhs, b.Bs, v.r, v.x, v.col, tol0, o.maxit, b.part, b.ticket,
+            mixed ? b.x64 : nullptr);
         h.launches += 2;
         r->started = true;
         joined = true;
@@ -241,14 +260,14 @@ lap_status launch(lap_server_s &S, GraphBatch &gb)
         // they already hold (same operands, same order: the same bits), and
         // only the joining (or restarted) columns take their first direction
         gb.rejoin = false;
-        bprecond<double>(h, b, v, false, gb.s);
-        kb_pupdate_join<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
+        bprecond<V>(h, b, v, false, gb.s);
+        kb_pupdate_join<V><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
             n, R, CT, o.prec == LAP_PREC_NONE ? v.r : v.z, v.p, v.col);
         kb_clear_join<<<1, 256, 0, gb.s>>>(R, v.col);
         h.launches += 2;
     }
     LAP_BCK(cudaGetLastError());
-    LAP_LTRY(capture_iterations<double>(h, b, v, gb.s, iterations_per_launch(S.opt, h)));
+    LAP_LTRY(capture_iterations<V>(h, b, v, gb.s, iterations_per_launch(S.opt, h)));
     LAP_BCK(cudaGraphLaunch(v.g, gb.s));
     h.launches += v.nodes;
     LAP_BCK(cudaMemcpyAsync(b.hcol, v.col, sizeof(BCol) * R, cudaMemcpyDeviceToHost, gb.s));
@@ -256,6 +275,11 @@ lap_status launch(lap_server_s &S, GraphBatch &gb)
     gb.launches += h.launches - l0;
     gb.launched = true;
     return LAP_OK;
+}
+
+lap_status launch(lap_server_s &S, GraphBatch &gb)
+{
+    return gb.mixed ? launch_t<float>(S, gb) : launch_t<double>(S, gb);
 }
 
 lap_status column_status(const BCol &c)
@@ -269,12 +293,16 @@ lap_status column_status(const BCol &c)
 }
 
 // Retire the requests of gb whose columns have all stopped (or that were
-// cancelled or timed out): write their solutions and complete them.
-lap_status retire(lap_server_s &S, GraphBatch &gb)
+// cancelled or timed out): refine or restart them, or write their solutions
+// and complete them.
+template <typename V>
+lap_status retire_t(lap_server_s &S, GraphBatch &gb)
 {
     lap_handle_s &h = *gb.h;
     BatchWork &b = *gb.w;
-    auto &v = b.v64;
+    auto &v = vecs<V>(b);
+    const bool mixed = std::is_same<V, float>::value;
+    const lap_options &o = h.m.opt;
     const int n = static_cast<int>(b.n), R = b.R, CT = b.CT;
     const int64_t l0 = h.launches;
     LAP_BCK(cudaEventSynchronize(gb.ev));
@@ -296,7 +324,7 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
             cancel = r->cancel;
         }
         const double age = std::chrono::duration<double>(now - r->arrival).count();
-        const bool late = h.m.opt.timeout_s > 0.0 && age > h.m.opt.timeout_s;
+        const bool late = o.timeout_s > 0.0 && age > o.timeout_s;
         lap_status forced = cancel ? LAP_ERR_CANCELLED : (late && !stopped) ? LAP_ERR_TIMEOUT : LAP_OK;
         if (!stopped && forced != LAP_OK) {
             kb_set_flags<<<1, 256, 0, gb.s>>>(R, r->c0, r->nrhs, v.col, kConverged);
@@ -306,24 +334,48 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
         if (stopped) done.push_back({r, forced});
     }
     if (done.empty()) return LAP_OK;
+    double *xs = b.x64;                  // the FP64 solution
+    if (mixed) {
+        // the ended inner solves' corrections into the FP64 solutions
+        for (const Done &d : done) {
+            kb_add_cols<V><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(n, R, CT, d.r->c0, d.r->nrhs, b.x64, v.x);
+            h.launches += 1;
+            int it = 0;
+            for (int j = d.r->c0; j < d.r->c0 + d.r->nrhs; ++j) it = std::max(it, gb.cols[j].iter);
+            d.r->iters += it;
+        }
+    } else {
+        xs = reinterpret_cast<double *>(b.v64.x);
+    }
     // true residuals of all columns (column states untouched) to r64 and tres
-    bspmm<double, 3>(h, b, h.L64, v.x, nullptr, b.r64, v.chunk, v.col, gb.s);
+    bspmm<double, 3>(h, b, h.L64, xs, nullptr, b.r64, b.v64.chunk, v.col, gb.s);
     std::vector<double> tres(static_cast<size_t>(R));
     LAP_BCK(cudaMemcpyAsync(tres.data(), b.tres, sizeof(double) * R, cudaMemcpyDeviceToHost, gb.s));
     LAP_BCK(cudaStreamSynchronize(gb.s));
-    // a request whose recurrence converged but whose true residual missed the
-    // tolerance restarts those columns from their true residual (x kept)
-    const double tol = h.m.opt.tol;
+    // columns whose true residual misses the tolerance go on from it: the next
+    // refinement step (mixed), or a restart of a converged recurrence (FP64)
+    const double tol = o.tol;
     std::vector<Done> fin;
     for (const Done &d : done) {
-        bool miss = false;
-        for (int j = d.r->c0; j < d.r->c0 + d.r->nrhs; ++j)
-            miss |= gb.cols[j].flag == kConverged && !(tres[j] <= tol);
-        if (d.forced == LAP_OK && miss && d.r->restarts < kServeRestarts) {
+        bool miss = false, again = false;
+        for (int j = d.r->c0; j < d.r->c0 + d.r->nrhs; ++j) {
+            miss |= !(tres[j] <= tol);
+            again |= gb.cols[j].flag == kConverged && !(tres[j] <= tol);
+        }
+        const bool go = mixed ? (miss && d.r->restarts < o.max_refine && d.r->iters < o.maxit)
+                              : (again && d.r->restarts < kServeRestarts);
+        if (d.forced == LAP_OK && go) {
             d.r->restarts += 1;
-            kb_restart_copy<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
-                n, R, CT, d.r->c0, d.r->nrhs, b.r64, v.r, v.col, b.tres, tol);
-            kb_restart_flags<<<1, 256, 0, gb.s>>>(R, d.r->c0, d.r->nrhs, v.col, b.tres, tol);
+            if (mixed) {
+                kb_refine_copy<V><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
+                    n, R, CT, d.r->c0, d.r->nrhs, b.r64, v.r, v.x, b.tres, tol);
+                kb_refine_flags<<<1, 256, 0, gb.s>>>(R, d.r->c0, d.r->nrhs, v.col, b.tres, tol, o.refine_tol,
+                                                     o.maxit);
+            } else {
+                kb_restart_copy<V><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
+                    n, R, CT, d.r->c0, d.r->nrhs, b.r64, v.r, v.col, b.tres, tol);
+                kb_restart_flags<<<1, 256, 0, gb.s>>>(R, d.r->c0, d.r->nrhs, v.col, b.tres, tol);
+            }
             h.launches += 2;
             gb.rejoin = true;
         } else {
@@ -335,11 +387,11 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
         gb.launches += h.launches - l0;
         return LAP_OK;
     }
-    kb_mean<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(n, R, CT, v.x, b.means, b.part, b.ticket);
+    kb_mean<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(n, R, CT, xs, b.means, b.part, b.ticket);
     h.launches += 1;
     for (const Done &d : done) {
         kb_scatter_range<double><<<bgrid(h, n, R, CT), kBThreads, 0, gb.s>>>(
-            n, R, CT, d.r->c0, d.r->nrhs, h.perm1, v.x, b.means, d.r->X);
+            n, R, CT, d.r->c0, d.r->nrhs, h.perm1, xs, b.means, d.r->X);
         h.launches += 1;
     }
     LAP_BCK(cudaStreamSynchronize(gb.s));
@@ -356,10 +408,14 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
             if (st == LAP_OK) st = cs;
             gb.owner[j] = nullptr;
         }
-        if (st == LAP_OK && !(rel <= h.m.opt.tol)) st = LAP_ERR_NO_CONVERGENCE;
+        // an inner solve that stops at its tolerance is converged; the outer
+        // test is the true residual
+        if (mixed && st == LAP_ERR_NO_CONVERGENCE && rel <= tol) st = LAP_OK;
+        if (st == LAP_OK && !(rel <= tol)) st = LAP_ERR_NO_CONVERGENCE;
         if (d.forced != LAP_OK) st = d.forced;
-        r->info.iterations = it;
-        r->info.restarts = r->restarts;
+        r->info.iterations = mixed ? r->iters : it;
+        r->info.refinements = mixed ? r->restarts : 0;
+        r->info.restarts = mixed ? 0 : r->restarts;
         r->info.relres = rel;
         r->info.relres_recurrence = 0.0;
         for (int j = r->c0; j < r->c0 + r->nrhs; ++j)
@@ -368,6 +424,11 @@ lap_status retire(lap_server_s &S, GraphBatch &gb)
         complete(S, r, st);
     }
     return LAP_OK;
+}
+
+lap_status retire(lap_server_s &S, GraphBatch &gb)
+{
+    return gb.mixed ? retire_t<float>(S, gb) : retire_t<double>(S, gb);
 }
 
 // A batch that failed on the device: complete its requests with `st` and drop it.

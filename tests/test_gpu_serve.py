@@ -249,3 +249,45 @@ def test_true_residual_restart():
         assert 0 <= info.restarts <= 4
     finally:
         S.close()
+
+
+def test_mixed_precision_requests_alone_and_in_the_mix(graphs):
+    """LAP_MIXED handles: FP32 columns refined per request against their FP64
+    true residual; converged to 1e-8, the same bits alone and in the mix, and
+    close to the oracle's FP64 solve."""
+    gs, _ = graphs
+    hs = [P.lap_setup(gs[0], seed=5, maxit=4000, precision="mixed"),
+          P.lap_setup(gs[1], seed=5, maxit=4000, precision="mixed")]
+    S = P.Server(max_slots=16, check_every=4)
+    try:
+        probe = _cols(gs[0].n, 2, seed=61)
+        st0, info0, X0 = _solve_alone(S, hs[0], probe)
+        assert st0 == 0, info0.as_dict()
+        assert info0.refinements >= 1
+        for j in range(2):
+            assert _relres(gs[0], probe[j], X0[j]) <= TOL
+        keep = []
+        for w in range(4):
+            i = w % 2
+            Bd = torch.as_tensor(_cols(gs[i].n, 1 + w, seed=900 + w), device="cuda")
+            Xd = torch.empty_like(Bd)
+            keep.append((i, Bd, Xd, S.submit(hs[i], Bd, Xd)))
+        Bp = torch.as_tensor(probe, device="cuda")
+        Xp = torch.empty_like(Bp)
+        rid = S.submit(hs[0], Bp, Xp)
+        st, info = S.wait(rid, 120.0)
+        assert st == 0
+        assert np.array_equal(Xp.cpu().numpy(), X0)
+        assert info.iterations == info0.iterations and info.refinements == info0.refinements
+        for i, Bd, Xd, r in keep:
+            st, info = S.wait(r, 120.0)
+            assert st == 0, info.as_dict()
+            B, X = Bd.cpu().numpy(), Xd.cpu().numpy()
+            for j in range(B.shape[0]):
+                assert _relres(gs[i], B[j], X[j]) <= TOL
+        ref = oracle.solve(gs[0], probe[0], "msp", seed=5)
+        L = laplacian(gs[0].adjacency())
+        bp = probe[0] - probe[0].mean()
+        assert np.linalg.norm(L @ (X0[0] - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+    finally:
+        S.close()

@@ -40,7 +40,7 @@ CPU_SAMPLE_NX = {"pegp_inner": 16, "msp": 24, "none": 24}   # oracle sample side
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current
 # kernel, scaled to the 128^3 workload (profiles/k_sell_f32_LH_grid3d96.md);
 # removed whenever the kernel changes.
-MEASURED_TRAFFIC = {"spmv_LH": 1.920e9}
+MEASURED_TRAFFIC = {}
 
 
 def parse():

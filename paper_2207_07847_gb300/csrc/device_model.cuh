@@ -50,6 +50,7 @@ template <typename V> struct DevCsr {
     int nslices = 0, nlong = 0;
     int64_t *sptr = nullptr;
     unsigned *lmask = nullptr;
+    int *rowperm = nullptr;            // row of each SELL slot (-1: none)
     int *eci = nullptr;
     V *ew = nullptr;
     int *lrow = nullptr, *lci = nullptr;

@@ -98,6 +98,7 @@ lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, Dev
         d.ci = share->ci;
         d.sptr = share->sptr;
         d.lmask = share->lmask;
+        d.rowperm = share->rowperm;
         d.eci = share->eci;
         d.lrow = share->lrow;
         d.lrp = share->lrp;
@@ -125,6 +126,7 @@ lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, Dev
         LAP_TRY(upload(h, &d.rp, c.rp));
         LAP_TRY(upload(h, &d.ci, c.ci));
         LAP_TRY(upload(h, &d.sptr, sl.sptr));
+        if (!sl.rowperm.empty()) LAP_TRY(upload(h, &d.rowperm, sl.rowperm));
         LAP_TRY(upload(h, &d.lmask, sl.longmask));
         LAP_TRY(upload(h, &d.eci, sl.eci));
         LAP_TRY(upload(h, &d.lrow, sl.lrow));
@@ -463,7 +465,7 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
         h.launches += 1;
         const int g = grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
 #define LAP_SELL(VEC)                                                                                   \
-    k_sell<V, MODE, VEC><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.eci, A.ew, A.nlong, A.lrow, \
+    k_sell<V, MODE, VEC><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.rowperm, A.eci, A.ew, A.nlong, A.lrow, \
                                               A.lchunk_ptr, A.chunk_part, x, y, bs, yres, st.sc, st.part,   \
                                               st.ticket)
         if (A.vec == 4) LAP_SELL(4);

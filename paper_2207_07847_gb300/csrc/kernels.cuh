@@ -292,12 +292,13 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
 }
 
 // SELL-32 matvec in edge-difference form: one warp per slice of 32 rows,
-// lane l owning row 32 s + l and reading its entries VEC at a time (see
-// make_sell for the layout); long rows add their chunk partials.
+// lane l owning the row of slot 32 s + l and reading its entries VEC at a
+// time (see make_sell for the layout); long rows add their chunk partials.
 template <typename V, int MODE, int VEC>
 __global__ void __launch_bounds__(kBlock)
 k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__restrict__ lmask,
-       const int *__restrict__ eci, const V *__restrict__ ew, int nlong, const int *__restrict__ lrow,
+       const int *__restrict__ rowperm, const int *__restrict__ eci, const V *__restrict__ ew, int nlong,
+       const int *__restrict__ lrow,
        const int *__restrict__ lchunk_ptr, const V *__restrict__ chunk_part,
        const V *__restrict__ x, V *__restrict__ y, const double *__restrict__ bs,
        double *__restrict__ yres, CgScalars *sc, double *part, unsigned *ticket)
@@ -310,8 +311,9 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
     const int ntask = nslices + nlong;
     for (int task = gwarp; task < ntask; task += nwarp) {          // warp-uniform
         if (task < nslices) {
-            const int row = task * 32 + lane;
-            const bool valid = row < n;
+            const int slot = task * 32 + lane;
+            const int row = rowperm ? rowperm[slot] : (slot < n ? slot : -1);
+            const bool valid = row >= 0;
             const int64_t base = sptr[task];
             const int width = static_cast<int>((sptr[task + 1] - base) >> 5);
             const V xi = valid ? x[row] : V(0);

@@ -57,6 +57,7 @@ struct HostSell {
     int vec = 1;                      // entries per lane group (1, 2 or 4): see make_sell
     std::vector<int64_t> sptr;        // [nslices + 1]
     std::vector<uint32_t> longmask;   // [nslices] lanes whose row is a long row
+    std::vector<int32_t> rowperm;     // [nslices * 32] row held by each slot (-1: none); empty: slot = row
     std::vector<int32_t> eci;
     std::vector<double> ew;
     std::vector<int32_t> lrow;        // long rows
@@ -72,7 +73,10 @@ struct HostSell {
 };
 
 // SELL-32 of A: slices of 32 rows, each padded to its longest row (rounded up
-// to a multiple of vec) and stored lane-interleaved in groups of vec entries:
+// to a multiple of vec) and stored lane-interleaved in groups of vec entries
+// (the rows sorted by decreasing length within windows of 8 slices when that
+// saves at least 5% of the padded size: slot 32 s + l then holds row
+// rowperm[32 s + l]):
 // entry j of lane l of slice s at sptr[s] + (j / vec) * 32 * vec + l * vec +
 // j % vec, so that a lane loads vec consecutive entries with one vector load.
 // Rows longer than long_threshold go to the long-row chunks (threshold 0:

@@ -600,11 +600,42 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
     S.lrp.assign(1, 0);
     S.lci.clear();
     S.lw.clear();
+    // slot order: within windows of kSigma slices the rows are sorted by
+    // decreasing length (stable), so that a slice pads to similar rows; long
+    // rows count as empty (their slot is masked)
+    const int64_t kWin = 32 * 8;
+    auto len = [&](int64_t r) {
+        const int64_t d = A.rp[r + 1] - A.rp[r];
+        return d > long_threshold ? int64_t(0) : d;
+    };
+    S.rowperm.assign(static_cast<size_t>(S.nslices) * 32, -1);
+    for (int64_t r = 0; r < n; ++r) S.rowperm[r] = static_cast<int32_t>(r);
+    auto slices_size = [&]() {
+        int64_t t = 0;
+        for (int64_t s0 = 0; s0 < n; s0 += 32) {
+            int64_t w = 0;
+            for (int64_t k = s0; k < std::min(n, s0 + 32); ++k) w = std::max(w, len(S.rowperm[k]));
+            t += 32 * w;
+        }
+        return t;
+    };
+    const int64_t unsorted = slices_size();
+    for (int64_t w0 = 0; w0 < n; w0 += kWin) {
+        const int64_t w1 = std::min(n, w0 + kWin);
+        std::stable_sort(S.rowperm.begin() + w0, S.rowperm.begin() + w1,
+                         [&](int32_t a, int32_t b) { return len(a) > len(b); });
+    }
+    // sorting pays only if it saves padding: else keep the rows in place (an
+    // empty rowperm: slot = row)
+    const bool sorted = slices_size() * 20 < unsorted * 19;
+    if (!sorted)
+        for (int64_t r = 0; r < n; ++r) S.rowperm[r] = static_cast<int32_t>(r);
     std::vector<int64_t> width(static_cast<size_t>(S.nslices), 0);
     for (int64_t s = 0; s < S.nslices; ++s) {
         for (int64_t lane = 0; lane < 32; ++lane) {
-            const int64_t r = 32 * s + lane;
-            if (r >= n) break;
+            const int64_t slot = 32 * s + lane;
+            if (slot >= n) break;
+            const int64_t r = S.rowperm[slot];
             const int64_t d = A.rp[r + 1] - A.rp[r];
             if (d > long_threshold) {
                 S.longmask[s] |= 1u << lane;
@@ -674,8 +705,9 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
     for (int64_t s = 0; s < S.nslices; ++s) {
         const int64_t w = (S.sptr[s + 1] - S.sptr[s]) / 32;
         for (int64_t lane = 0; lane < 32; ++lane) {
-            const int64_t r = 32 * s + lane;
-            const bool real = r < n && !((S.longmask[s] >> lane) & 1u);
+            const int64_t slot = 32 * s + lane;
+            const int64_t r = slot < n ? S.rowperm[slot] : -1;
+            const bool real = r >= 0 && !((S.longmask[s] >> lane) & 1u);
             const int64_t d = real ? A.rp[r + 1] - A.rp[r] : 0;
             for (int64_t j = 0; j < w; ++j) {
                 const int64_t q = S.sptr[s] + (j / vec) * 32 * vec + lane * vec + j % vec;
@@ -683,11 +715,12 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
                     S.eci[q] = A.ci[A.rp[r] + j];
                     S.ew[q] = A.w[A.rp[r] + j];
                 } else {
-                    S.eci[q] = static_cast<int32_t>(r < n ? r : 0);   // weight 0: no contribution
+                    S.eci[q] = static_cast<int32_t>(r >= 0 ? r : 0);   // weight 0: no contribution
                 }
             }
         }
     }
+    if (!sorted) S.rowperm.clear();
 }
 
 // ---------------------------------------------------------------------------

@@ -340,3 +340,54 @@ def test_full_size_grid3d_solve_properties():
         res = bp - (deg * xg - (A @ xg.unsqueeze(1)).squeeze(1))
         assert float(torch.linalg.norm(res) / torch.linalg.norm(bp)) <= 1e-8
         hh.close()
+
+
+def _hub_graph():
+    """Six hubs in a path, each with its own leaves (2,500, 2,500, 8,000,
+    8,000, 300 and 300): every hub's aggregate holds all its leaves, so the
+    sweeps meet aggregates of thousands of members (eliminated by a warp) and
+    subtrees too large for shared memory (run in global memory)."""
+    sizes = [2500, 2500, 8000, 8000, 300, 300]
+    u, v = [], []
+    nxt = len(sizes)
+    for hb, k in enumerate(sizes):
+        u += [hb] * k
+        v += list(range(nxt, nxt + k))
+        nxt += k
+    u += list(range(len(sizes) - 1))
+    v += list(range(1, len(sizes)))
+    w = gg.edge_weights(len(u), "loguniform", 1e-2, 1e2, seed=7)
+    return gg.from_edges(nxt, np.array(u), np.array(v), w, "hubs")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hub_aggregates_and_oversized_tiles(precision):
+    g = _hub_graph()
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=17)
+    ops = oracle.expanded_operators(ho, 0.8, with_LG=False)
+    h = P.lap_setup(g, seed=17, mu=0.8, precision=precision)
+    info = P.lap_get_hierarchy_info(h)
+    agg, _, _ = P.lap_get_aggregates(h, 1)
+    assert np.bincount(agg).max() >= 8000
+    r = gg.rhs(g.n, seed=5)
+    # the sparsifier solve itself, by its residual (Section 3.3)
+    rt = ops.Pmu.T @ (r - r.mean())
+    yt = dev(np.zeros(ops.ntilde))
+    P.lap_msp_solve(h, dev(rt), yt)
+    y = host(yt)
+    assert np.linalg.norm(ops.LT @ y - rt) <= 1e-11 * (abs(ops.LT) @ np.abs(y)).max() * np.sqrt(ops.ntilde)
+    # the preconditioner against the oracle: L_T's diagonal spans 1e-2..9e4
+    # here, and the oracle's own sparse solve moves by 7e-10 (relative) under
+    # one step of iterative refinement, so agreement is asked to 1e-8
+    z = dev(np.zeros(g.n))
+    P.lap_precond_apply(h, dev(r), z)
+    want = oracle.OraclePreconditioner("msp", ops)(r)
+    assert np.linalg.norm(host(z) - want) <= 1e-8 * np.linalg.norm(want), info
+    b = dev(gg.rhs(g.n, seed=6))
+    x, inf = solve_gpu(h, b)
+    assert inf.status == 0, inf.as_dict()
+    ref = oracle.solve(g, host(b), "msp", mu=0.8, seed=17)
+    assert abs(inf.iterations - ref.iters) <= max(2, round(0.03 * ref.iters)) or precision == "mixed"
+    L = laplacian(g.adjacency())
+    bp = host(b) - host(b).mean()
+    assert np.linalg.norm(L @ (host(x) - ref.x)) <= 2e-8 * np.linalg.norm(bp)

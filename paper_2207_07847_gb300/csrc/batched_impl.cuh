@@ -152,17 +152,17 @@ void bprecond(const lap_handle_s &h, const BatchWork &b, BatchVectors<V> &v, boo
     if (update)
         kb_up<V, 1><<<bgrid(h, L0.nagg, R, CT), kBThreads, 0, s>>>(
             L0.nagg, R, CT, L0.seg, L0.inv, L0.lcf, v.x, v.r, v.p, v.q, v.A, v.A + M.off[1] * RR,
-            M.gamma[0], nullptr, v.col, b.part, b.ticket);
+            M.gamma[0], nullptr, v.col, b.part, b.ticket, L0.nbig, L0.big);
     else
         kb_up<V, 2><<<bgrid(h, L0.nagg, R, CT), kBThreads, 0, s>>>(
             L0.nagg, R, CT, L0.seg, L0.inv, L0.lcf, v.x, v.r, v.p, v.q, v.A, v.A + M.off[1] * RR,
-            M.gamma[0], nullptr, v.col, b.part, b.ticket);
+            M.gamma[0], nullptr, v.col, b.part, b.ticket, L0.nbig, L0.big);
     for (int k = 1; k + 1 < l; ++k) {
         const auto &Lk = M.lev[k];
         V *a = v.A + M.off[k] * RR;
         kb_up<V, 0><<<bgrid(h, Lk.nagg, R, CT), kBThreads, 0, s>>>(
             Lk.nagg, R, CT, Lk.seg, Lk.inv, Lk.lcf, nullptr, a, nullptr, nullptr, a,
-            v.A + M.off[k + 1] * RR, M.gamma[k], nullptr, v.col, nullptr, nullptr);
+            v.A + M.off[k + 1] * RR, M.gamma[k], nullptr, v.col, nullptr, nullptr, Lk.nbig, Lk.big);
     }
     const size_t ot = static_cast<size_t>(M.off[l - 1]) * RR;
     kb_coarse<V><<<bgrid(h, M.ntop, R, CT), kBThreads, 0, s>>>(M.ntop, R, M.G, v.A + ot, v.Y + ot,
@@ -171,11 +171,12 @@ void bprecond(const lap_handle_s &h, const BatchWork &b, BatchVectors<V> &v, boo
         const auto &Lk = M.lev[k];
         kb_down<V, false><<<bgrid(h, Lk.nagg, R, CT), kBThreads, 0, s>>>(
             Lk.n, Lk.nagg, R, CT, Lk.seg, v.A + M.off[k] * RR, v.Y + M.off[k + 1] * RR,
-            v.Y + M.off[k] * RR, V(1), static_cast<V>(M.c[k]), nullptr, v.col, nullptr, nullptr);
+            v.Y + M.off[k] * RR, V(1), static_cast<V>(M.c[k]), nullptr, v.col, nullptr, nullptr, Lk.nbig,
+            Lk.big);
     }
     kb_down<V, true><<<bgrid(h, L0.nagg, R, CT), kBThreads, 0, s>>>(
         n, L0.nagg, R, CT, L0.seg, v.A, v.Y + M.off[1] * RR, v.z, V(1), V(1), v.r, v.col, b.part,
-        b.ticket);
+        b.ticket, L0.nbig, L0.big);
 }
 
 template <typename V>

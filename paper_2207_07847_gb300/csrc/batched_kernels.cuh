@@ -261,19 +261,96 @@ kb_spmm(int n, int R, int CT, const int *__restrict__ rp, const int *__restrict_
 // MODE 0: level k >= 2 in place (a -> delta); MODE 1: finest level with the CG
 // step (x += alpha p, r -= alpha q for active columns), delta_1 -> dout,
 // reduces ||r||^2, sum r -> convergence per column; MODE 2: finest, no step.
+// Aggregates with more than kBatchBigAgg members (big[0..nbig), hubs of
+// power-law graphs) are taken by a whole block each: the row groups split
+// the members, the per-column sums meet in shared memory.
 template <typename V, int MODE>
 __global__ void __launch_bounds__(kBThreads)
 kb_up(int nagg, int R, int CT, const int *__restrict__ seg, const V *__restrict__ inv,
       const V *__restrict__ lcf, V *__restrict__ x, V *r, const V *__restrict__ p,
       const V *__restrict__ q, V *dout, V *anext, V gamma, const V *fnext, BCol *col, double *part,
-      unsigned *ticket)
+      unsigned *ticket, int nbig, const int *__restrict__ big)
 {
     __shared__ double tot[512];
+    __shared__ V bred[3][kBThreads];
+    __shared__ V bsol[2][kBThreads];
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
     double acc[2][8];
     for (int j = 0; j < 8; ++j) acc[0][j] = acc[1][j] = 0.0;
+    for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const int J = big[bi];
+        const int b0 = seg[J], e = seg[J + 1];
+        const V *cf = inv + 4 * J;
+        const V *lc = lcf + 3 * (b0 - 2 * J);
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            if (MODE == 1) {
+                const bool act = bactive(col, c);
+                const V al = act ? (V)col[c].alpha : V(0);
+                if (act)
+                    for (int u = b0 + o; u < e; u += S) {
+                        const size_t k = (size_t)u * R + c;
+                        x[k] += al * p[k];
+                        r[k] -= al * q[k];
+                    }
+                __syncthreads();
+            }
+            V sm = V(0), ha = V(0), hb = V(0);
+            for (int t = b0 + 2 + o; t < e; t += S) {
+                const V al = r[(size_t)t * R + c];
+                const V *cc = lc + 3 * (t - b0 - 2);
+                sm += al;
+                ha += cc[0] * al;
+                hb += cc[1] * al;
+                if (MODE != 0) {
+                    acc[0][jj] += (double)al * al;
+                    acc[1][jj] += (double)al;
+                }
+            }
+            if (o == 0) {
+                const V aa = r[(size_t)b0 * R + c], ab = r[(size_t)(b0 + 1) * R + c];
+                sm += aa + ab;
+                ha += aa;
+                hb += ab;
+                if (MODE != 0) {
+                    acc[0][jj] += (double)aa * aa + (double)ab * ab;
+                    acc[1][jj] += (double)aa + (double)ab;
+                }
+            }
+            bred[0][threadIdx.x] = sm;
+            bred[1][threadIdx.x] = ha;
+            bred[2][threadIdx.x] = hb;
+            __syncthreads();
+            for (int st = S / 2; st > 0; st >>= 1) {
+                if (o < st)
+                    for (int k = 0; k < 3; ++k) bred[k][threadIdx.x] += bred[k][threadIdx.x + st * CT];
+                __syncthreads();
+            }
+            if (o == 0) {
+                V da, db;
+                pair_solve(cf, bred[1][cl], bred[2][cl], da, db);
+                bsol[0][cl] = da;
+                bsol[1][cl] = db;
+                V nx = gamma * bred[0][cl];
+                if (fnext) nx += fnext[(size_t)J * R + c];
+                anext[(size_t)J * R + c] = nx;
+            }
+            __syncthreads();
+            const V da = bsol[0][cl], db = bsol[1][cl];
+            for (int t = b0 + 2 + o; t < e; t += S) {
+                const V *cc = lc + 3 * (t - b0 - 2);
+                dout[(size_t)t * R + c] = r[(size_t)t * R + c] * cc[2] + cc[0] * da + cc[1] * db;
+            }
+            if (o == 0) {
+                dout[(size_t)b0 * R + c] = da;
+                dout[(size_t)(b0 + 1) * R + c] = db;
+            }
+            __syncthreads();
+        }
+    }
     for (int J = blockIdx.x * S + o; J < nagg; J += gridDim.x * S) {
         const int b0 = seg[J], e = seg[J + 1];
+        if (e - b0 > kBatchBigAgg) continue;
         const V *cf = inv + 4 * J;
         const V *lc = lcf + 3 * (b0 - 2 * J);
         for (int jj = 0; jj < R / CT; ++jj) {
@@ -359,13 +436,31 @@ template <typename V, bool FINEST>
 __global__ void __launch_bounds__(kBThreads)
 kb_down(int n, int nagg, int R, int CT, const int *__restrict__ seg, const V *__restrict__ delta,
         const V *__restrict__ parent, V *__restrict__ out, V pc, V dc, const V *__restrict__ r,
-        BCol *col, double *part, unsigned *ticket)
+        BCol *col, double *part, unsigned *ticket, int nbig, const int *__restrict__ big)
 {
     __shared__ double tot[512];
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
     double acc[2][8];
     for (int j = 0; j < 8; ++j) acc[0][j] = acc[1][j] = 0.0;
+    // large aggregates: a block each, the row groups splitting the members
+    for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const int J = big[bi];
+        for (int jj = 0; jj < R / CT; ++jj) {
+            const int c = cl + jj * CT;
+            const V base = pc * parent[(size_t)J * R + c];
+            for (int u = seg[J] + o; u < seg[J + 1]; u += S) {
+                const size_t k = (size_t)u * R + c;
+                const V z = base + dc * delta[k];
+                out[k] = z;
+                if (FINEST) {
+                    acc[0][jj] += (double)z;
+                    acc[1][jj] += (double)r[k] * (double)z;
+                }
+            }
+        }
+    }
     for (int J = blockIdx.x * S + o; J < nagg; J += gridDim.x * S) {
+        if (seg[J + 1] - seg[J] > kBatchBigAgg) continue;
         for (int jj = 0; jj < R / CT; ++jj) {
             const int c = cl + jj * CT;
             const V base = pc * parent[(size_t)J * R + c];

@@ -72,6 +72,8 @@ template <typename V> struct DevMspLevel {
     int64_t off = 0;            // expanded offset of this level (tree order)
     int *seg = nullptr;         // shared between precisions
     V *inv = nullptr, *lcf = nullptr;
+    int nbig = 0;               // aggregates of more than kBatchBigAgg members ...
+    int *big = nullptr;         // ... their indices (batched kernels: a block each)
 };
 
 template <typename V> struct DevMsp {

@@ -163,6 +163,13 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
         LAP_TRY(upload(h, &L.inv, S.inv));
         LAP_TRY(upload(h, &L.lcf, S.lcf));
         d.gamma[k] = static_cast<V>(m.c[k + 1] / m.c[k]);
+        {
+            std::vector<int32_t> big;
+            for (int64_t J = 0; J < S.nagg; ++J)
+                if (S.seg[J + 1] - S.seg[J] > kBatchBigAgg) big.push_back(static_cast<int32_t>(J));
+            L.nbig = static_cast<int>(big.size());
+            if (!big.empty()) LAP_TRY(upload(h, &L.big, big));
+        }
     }
     d.c.assign(m.c.begin(), m.c.end());
     d.ntop = static_cast<int>(m.lev[l - 1].n);

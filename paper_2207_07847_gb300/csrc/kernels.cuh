@@ -494,6 +494,7 @@ __device__ __forceinline__ V warp_eliminate(V *a, int cnt, const V *lc, const V 
 }
 
 constexpr int kBigAgg = 32;   // aggregates with more members are eliminated by a warp
+constexpr int kBatchBigAgg = 64;   // batched sweeps: aggregates with more members take a block
 
 // Upward elimination of one level of a tile, in place: aggregate jl (of na)
 // holds the members [sg[jl] - sbase, sg[jl + 1] - sbase) of a, its pair

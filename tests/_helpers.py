@@ -3,6 +3,8 @@ import os
 
 import numpy as np
 
+import graphgen as gg
+
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -47,3 +49,21 @@ def kappa_nonzero(A, B, zero=1e-9):
     ev = pencil_eigs(A, B)
     evp = ev[ev > zero]
     return evp.max() / evp.min()
+
+
+def hub_graph():
+    """Six hubs in a path, each with its own leaves (2,500, 2,500, 8,000,
+    8,000, 300 and 300): every hub's aggregate holds all its leaves, so the
+    sweeps meet aggregates of thousands of members (eliminated by a warp) and
+    subtrees too large for shared memory (run in global memory)."""
+    sizes = [2500, 2500, 8000, 8000, 300, 300]
+    u, v = [], []
+    nxt = len(sizes)
+    for hb, k in enumerate(sizes):
+        u += [hb] * k
+        v += list(range(nxt, nxt + k))
+        nxt += k
+    u += list(range(len(sizes) - 1))
+    v += list(range(1, len(sizes)))
+    w = gg.edge_weights(len(u), "loguniform", 1e-2, 1e2, seed=7)
+    return gg.from_edges(nxt, np.array(u), np.array(v), w, "hubs")

@@ -35,7 +35,7 @@ def _cols(n, k, seed):
     return np.stack([gg.rhs(n, seed=seed + j) for j in range(k)])     # (k, n) = column-major n x k
 
 
-def _check_columns(g, B, X, infos, tol=1e-8):
+def _check_columns(g, B, X, infos, tol=1e-8, floor=1e-15):
     L = laplacian(g.adjacency())
     for j in range(B.shape[0]):
         b = B[j] - B[j].mean()
@@ -46,7 +46,7 @@ def _check_columns(g, B, X, infos, tol=1e-8):
         rel = np.linalg.norm(b - L @ X[j]) / nb
         assert rel <= tol, (j, rel, infos[j].as_dict())
         assert infos[j].status == 0 and infos[j].relres <= tol
-        assert abs(infos[j].relres - rel) <= 1e-3 * rel + 1e-15
+        assert abs(infos[j].relres - rel) <= 1e-3 * rel + floor
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -125,3 +125,24 @@ def test_batched_more_than_256_columns():
     st, infos = P.lap_pcg_solve_batched([h], [Bd], [Xd])
     assert st == 0 and len(infos) == 300
     _check_columns(g, B, Xd.cpu().numpy(), infos)
+
+
+def test_batched_hub_aggregates():
+    """Aggregates of thousands of members (a block each in the batched sweeps)."""
+    from _helpers import hub_graph
+    g = hub_graph()
+    B = _cols(g.n, 9, seed=71)
+    for precision in ("fp64", "mixed"):
+        h = P.lap_setup(g, seed=17, mu=0.8, precision=precision)
+        Bd = torch.as_tensor(B, device="cuda")
+        Xd = torch.empty_like(Bd)
+        st, infos = P.lap_pcg_solve_batched([h], [Bd], [Xd])
+        assert st == 0, precision
+        # the hubs' rows carry |L| |x| about 1e6 times ||Pi b||: true residuals
+        # recomputed in another summation order differ by up to ~1e-10 there
+        _check_columns(g, B, Xd.cpu().numpy(), infos, floor=1e-9)
+        x1 = torch.empty_like(Bd[0])
+        single = P.lap_pcg_solve(h, Bd[0], x1)
+        L = laplacian(g.adjacency())
+        bp = B[0] - B[0].mean()
+        assert np.linalg.norm(L @ (Xd[0].cpu().numpy() - x1.cpu().numpy())) <= 2e-8 * np.linalg.norm(bp)

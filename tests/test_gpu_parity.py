@@ -23,6 +23,8 @@ import graphgen as gg
 import oracle
 from oracle.expanded import laplacian
 
+from _helpers import hub_graph
+
 torch = pytest.importorskip("torch")
 P = pytest.importorskip("paper_2207_07847_gb300")
 
@@ -342,27 +344,9 @@ def test_full_size_grid3d_solve_properties():
         hh.close()
 
 
-def _hub_graph():
-    """Six hubs in a path, each with its own leaves (2,500, 2,500, 8,000,
-    8,000, 300 and 300): every hub's aggregate holds all its leaves, so the
-    sweeps meet aggregates of thousands of members (eliminated by a warp) and
-    subtrees too large for shared memory (run in global memory)."""
-    sizes = [2500, 2500, 8000, 8000, 300, 300]
-    u, v = [], []
-    nxt = len(sizes)
-    for hb, k in enumerate(sizes):
-        u += [hb] * k
-        v += list(range(nxt, nxt + k))
-        nxt += k
-    u += list(range(len(sizes) - 1))
-    v += list(range(1, len(sizes)))
-    w = gg.edge_weights(len(u), "loguniform", 1e-2, 1e2, seed=7)
-    return gg.from_edges(nxt, np.array(u), np.array(v), w, "hubs")
-
-
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_hub_aggregates_and_oversized_tiles(precision):
-    g = _hub_graph()
+    g = hub_graph()
     ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=17)
     ops = oracle.expanded_operators(ho, 0.8, with_LG=False)
     h = P.lap_setup(g, seed=17, mu=0.8, precision=precision)

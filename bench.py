@@ -36,11 +36,12 @@ WORKLOAD = {
     "nx": 128, "wlo": 1e-3, "whi": 1e3, "wseed": 3, "prec": "pegp_inner", "mu": 0.8,
     "tol": 1e-8, "inner_tol": 1e-1, "inner_maxit": 12, "setup_seed": 1,
 }
-CPU_SAMPLE_NX = {"pegp_inner": 16, "msp": 24, "none": 24}   # oracle sample sides
+CPU_SAMPLE_NX = {"pegp_inner": 16, "pegp_exact": 16, "msp": 24, "none": 24}   # oracle sample sides
+FP64_ALU_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (no measured figure exists)
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current
 # kernel, scaled to the 128^3 workload (profiles/k_sell_f32_LH_grid3d96.md);
 # removed whenever the kernel changes.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {"spmv_LH": 1.841e9}
 
 
 def parse():
@@ -55,7 +56,11 @@ def parse():
                          "iterations, nothing timed or printed")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=WORKLOAD["nx"], help="grid side (128 = the workload)")
-    ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["pegp_inner", "msp", "none"])
+    ap.add_argument("--prec", default=WORKLOAD["prec"],
+                    choices=["pegp_inner", "msp", "none", "pegp_exact"],
+                    help="pegp_exact: profiling runs only (small grids)")
+    ap.add_argument("--exact-side", type=int, default=64,
+                    help="side of the 2D grid of the exact-PEGP line (0: skip it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--powerlaw-n", type=int, default=1 << 20,
                     help="vertices of the Chung-Lu line (0: skip it)")
@@ -217,6 +222,9 @@ def bench_ours(args, rank, world):
         torch.distributed.barrier()
     P.lib()
     P.set_torch_allocator()
+    if args.prec == "pegp_exact" and not args.profile:
+        raise SystemExit("--prec pegp_exact is for profiling runs (--profile); the exact PEGP "
+                         "is timed on the small 2D grid line (--exact-side)")
 
     g = gg.grid3d(args.nx, weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
                   seed=WORKLOAD["wseed"])
@@ -311,12 +319,16 @@ def bench_ours(args, rank, world):
                          seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"], maxit=30000)
         ms_mm, inf_mm, lat_mm = timed("mixed", hh=hm, k_steps=A, w_steps=1)
         ms_mf, inf_mf, lat_mf = timed("fp64", hh=hm, k_steps=A, w_steps=0)
+        # Lanczos estimate of B L's extreme eigenvalues from the last FP64 solve
+        k_l, lo_l, hi_l = P.lap_estimate_condition(hm)
         msp = {"mixed": {"value": whole_job_rate(A, world, ms_mm), "unit": "solves/s",
                          "latency_ms": {"p50": pct(lat_mm, 0.5), "p99": pct(lat_mm, 0.99)},
                          "iterations": statistics.median(i.iterations for i in inf_mm)},
                "fp64": {"value": whole_job_rate(A, world, ms_mf), "unit": "solves/s",
                         "latency_ms": {"p50": pct(lat_mf, 0.5), "p99": pct(lat_mf, 0.99)},
-                        "iterations": statistics.median(i.iterations for i in inf_mf)},
+                        "iterations": statistics.median(i.iterations for i in inf_mf),
+                        "lanczos": {"steps": k_l, "lambda_min": lo_l, "lambda_max": hi_l,
+                                    "kappa": hi_l / lo_l}},
                "failed": [i.as_dict() for i in inf_mm + inf_mf if i.status != 0]}
         hm.close()
     value = whole_job_rate(K, world, ms_mixed)
@@ -359,6 +371,8 @@ def bench_ours(args, rank, world):
         "failed_solves": failed,
     }
     h.close()
+    if args.exact_side > 0:
+        result["pegp_exact"] = bench_pegp_exact(args, dev, world)
     if args.powerlaw_n > 0:
         result["powerlaw"] = bench_powerlaw(args, dev, world)
     if args.batched_scale > 0:
@@ -413,6 +427,61 @@ def bench_powerlaw(args, dev, world):
                           "iterations": [i.iterations for i in infos],
                           "relres_max": max(i.relres for i in infos),
                           "failed": sum(1 for i in infos if i.status != 0)}
+    h.close()
+    return out
+
+
+def bench_pegp_exact(args, dev, world):
+    """The small workload solved the paper's way: 2D grid (64 x 64, 4-neighbour,
+    weights uniform in [1, 2]) coarsened to <= 32 vertices, PEGP applied
+    exactly (dense inverse of the scaled L_H, built on the device at setup),
+    mu = 1/sqrt(n), all FP64, one N(0,1) right-hand side per solve.  Also the
+    Lanczos estimate of kappa(L_H^+ L_Gt) and the dense matvec's rates: FP64
+    is bound by the FP64 pipe (one FMA per 8-byte entry), FP32 by HBM."""
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+    side = args.exact_side
+    g = gg.grid2d(side, weights="uniform", lo=1.0, hi=2.0, seed=1)
+    mu = 1.0 / math.sqrt(g.n)
+    t0 = time.perf_counter()
+    h = P.lap_setup(g, prec="pegp_exact", mu=mu, precision="mixed", seed=WORKLOAD["setup_seed"],
+                    tol=WORKLOAD["tol"], maxit=1000)
+    setup_s = time.perf_counter() - t0
+    info_h = P.lap_get_hierarchy_info(h)
+    P.lap_update_options(h, precision="fp64")
+    stream = torch.cuda.current_stream()
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    bs = [torch.as_tensor(gg.rhs(g.n, seed=900 + i), device=dev) for i in range(23)]
+    for b in bs[:3]:
+        P.lap_pcg_solve(h, b, x)                                     # warm-up
+    ranks_barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [P.lap_pcg_solve(h, b, x) for b in bs[3:]]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    k_l, lo_l, hi_l = P.lap_estimate_condition(h)
+    nt = info_h["ntilde"]
+    m64, b64 = P.lap_kernel_bench(h, "pegp_gemv", 0, 20)
+    m32, b32 = P.lap_kernel_bench(h, "pegp_gemv", 1, 20)
+    out = {"workload": f"grid2d_{side}x{side}_uniform[1,2]_PEGP_exact_mu1/sqrt(n)_fp64", "n": g.n,
+           "ntilde": nt, "levels": info_h["levels"], "mu": mu, "setup_s": round(setup_s, 3),
+           "value": whole_job_rate(len(infos), world, ms), "unit": "solves/s",
+           "ms_per_solve": ms / len(infos),
+           "iterations": [i.iterations for i in infos][:5],
+           "relres_max": max(i.relres for i in infos),
+           "failed": sum(1 for i in infos if i.status != 0),
+           "lanczos": {"steps": k_l, "lambda_min": lo_l, "lambda_max": hi_l, "kappa": hi_l / lo_l},
+           "dense_matvec": {
+               "fp64": {"us": round(m64 * 1e3, 2), "GB/s": round(b64 / (m64 * 1e-3) / 1e9, 1),
+                        "bound": "alu", "TFLOP/s": round(2.0 * nt * nt / (m64 * 1e-3) / 1e12, 3),
+                        "peak_TFLOP/s": FP64_ALU_PEAK_TFLOPS, "peak_kind": "nominal"},
+               "fp32": {"us": round(m32 * 1e3, 2), "GB/s": round(b32 / (m32 * 1e-3) / 1e9, 1),
+                        "bound": "hbm"}}}
     h.close()
     return out
 

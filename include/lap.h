@@ -63,7 +63,10 @@ typedef enum lap_prec {
     LAP_PREC_NONE = 0,        /* B = Pi: plain conjugate gradients            */
     LAP_PREC_MSP = 1,         /* M = L_T^+, multilevel sparsifier (Sec. 3.3)  */
     LAP_PREC_PEGP_INNER = 2,  /* M ~= L_H^+ by an inner CG on L_H with MSP     */
-    LAP_PREC_PEGP_EXACT = 3   /* M = L_H^+ as a dense matrix (small graphs)   */
+    LAP_PREC_PEGP_EXACT = 3   /* M = L_H^+ applied exactly: a dense inverse of
+                                 the scaled L_H, computed on the device at
+                                 setup (ntilde <= 16384, else setup returns
+                                 LAP_ERR_UNSUPPORTED)                          */
 } lap_prec;
 
 typedef enum lap_precision {
@@ -72,6 +75,12 @@ typedef enum lap_precision {
                                  FP64 dots, scalars, projection, coarsest
                                  solve and iterative-refinement residuals    */
 } lap_precision;
+
+/* Outer Krylov method of lap_pcg_solve. */
+typedef enum lap_krylov {
+    LAP_KRYLOV_CG = 0,        /* preconditioned CG (flexible for PEGP_INNER)     */
+    LAP_KRYLOV_FGMRES = 1     /* flexible GMRES(restart), right preconditioning  */
+} lap_krylov;
 
 typedef struct lap_options {
     int32_t prec;          /* lap_prec (default LAP_PREC_MSP)                     */
@@ -101,7 +110,11 @@ typedef struct lap_options {
     int32_t stall_window;  /* LAP_MIXED: an FP32 inner solve returns to refinement
                               once its residual has set no new minimum for this
                               many iterations (default 1000; 0 = never)         */
-    int32_t reserved[5];
+    int32_t krylov;        /* outer method: LAP_KRYLOV_CG (default) or
+                              LAP_KRYLOV_FGMRES (the paper's, Section 4; LAP_FP64
+                              solves only)                                       */
+    int32_t restart;       /* FGMRES cycle length m, 1..128 (default 30)          */
+    int32_t reserved[3];
 } lap_options;
 
 typedef struct lap_solve_info {
@@ -158,7 +171,11 @@ lap_status lap_set_allocator(lap_alloc_fn alloc, lap_free_fn release, void *ctx)
  * (Section 2.2), the sparsifier T (Section 3.3) and, for the PEGP
  * preconditioners, H (Section 3.2), and uploads everything to the current
  * CUDA device on `stream`.  Requires n >= 2.  opts == NULL uses the defaults.
- * On success *out owns device memory until lap_destroy.
+ * On success *out owns device memory until lap_destroy.  LAP_PREC_PEGP_EXACT
+ * with two or more levels also inverts the expanded Laplacian densely
+ * (ntilde^2 doubles, plus ntilde^2 floats for LAP_MIXED; O(ntilde^3) FP64
+ * work): LAP_ERR_UNSUPPORTED if ntilde > 16384, LAP_ERR_BREAKDOWN if a pivot
+ * of the elimination is not positive.
  */
 lap_status lap_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                      const double *w, const lap_options *opts, void *stream,
@@ -169,7 +186,8 @@ void lap_destroy(lap_handle h);
 
 /*
  * Change the solve-time options of a handle: tol, maxit, inner_tol,
- * inner_maxit, refine_tol, max_refine, check_every, timeout_s and precision.
+ * inner_maxit, refine_tol, max_refine, check_every, timeout_s, stall_window,
+ * krylov, restart and precision.
  * precision may switch to LAP_MIXED only if the handle was set up with
  * LAP_MIXED (FP32 copies exist); switching to LAP_FP64 is always allowed.
  * Setup-time fields (prec, mu, coarse_max, max_levels, seed, order_random,
@@ -184,6 +202,7 @@ lap_status lap_update_options(lap_handle h, const lap_options *opts);
  *                                                  upward band of the sweep
  *   kernel 4: the sweep's coarse tail    kernel 5: the last downward band
  *             (one block)                          (z and its reductions)
+ *   kernel 6: the exact PEGP dense matvec y~ = G r~ (LAP_PREC_PEGP_EXACT)
  * in FP64 (precision 0) or FP32 (precision 1, LAP_MIXED handles).  Runs `reps`
  * back-to-back launches (sequences for kernel 2) on the handle's stream
  * timed by CUDA events and writes the mean milliseconds per launch and the
@@ -245,8 +264,11 @@ lap_status lap_pegp_apply(lap_handle h, const double *d_xt, double *d_yt, void *
 /* --- solves --- */
 
 /*
- * Solve L x = b by preconditioned CG (flexible CG for PEGP_INNER) to the
- * handle's tolerance.  d_b and d_x are device n-vectors (may not alias).
+ * Solve L x = b by preconditioned CG (flexible CG for PEGP_INNER), or with
+ * krylov = LAP_KRYLOV_FGMRES by flexible GMRES(restart) with right
+ * preconditioning (FP64 only, else LAP_ERR_UNSUPPORTED; iterations count the
+ * products with L, restarts the cycles after the first), to the handle's
+ * tolerance.  d_b and d_x are device n-vectors (may not alias).
  * Synchronises `stream` before returning.  info may be NULL.  Returns LAP_OK
  * on convergence, LAP_ERR_NO_CONVERGENCE / LAP_ERR_BREAKDOWN /
  * LAP_ERR_TIMEOUT with the best x so far otherwise.
@@ -262,6 +284,36 @@ lap_status lap_pcg_solve(lap_handle h, const double *d_b, double *d_x, void *str
  * number recorded to *count (capped at the handle's maxit).
  */
 lap_status lap_get_history(lap_handle h, double *h_out, int32_t cap, int32_t *count);
+
+/*
+ * CG coefficients of the first CG run of the handle's last solve (the whole
+ * solve unless it restarted; for LAP_MIXED the first FP32 inner solve): the
+ * step lengths alpha_j (x += alpha_j p_j) and the direction coefficients
+ * beta_j (p_(j+1) = Pi z_(j+1) + beta_j p_j), j = 0..count-1, with beta of the
+ * last step reported as 0.  Writes at most cap values to each of the host
+ * arrays h_alpha and h_beta (either may be NULL) and the run's length to
+ * *count.  LAP_ERR_INVALID_ARG for a host-only handle.
+ */
+lap_status lap_get_lanczos(lap_handle h, double *h_alpha, double *h_beta, int32_t cap,
+                           int32_t *count);
+
+/*
+ * Extreme eigenvalues of the preconditioned operator B L on the complement of
+ * the constants, estimated from the last solve's first CG run by the Lanczos
+ * connection: the k x k tridiagonal with diagonal 1/alpha_j +
+ * beta_(j-1)/alpha_(j-1) and off-diagonal sqrt(beta_j)/alpha_j has
+ * eigenvalues (Ritz values) inside [lambda_min, lambda_max] of B L that
+ * approach its extremes as k grows; lambda_max / lambda_min estimates, from
+ * below, the condition number the paper bounds: the nonzero eigenvalues of
+ * B L are those of M L_Gt, which for the exact PEGP lie in [1 - rho, 1]
+ * (Section 3.2, spectral equivalence of Gt and H) and for MSP below the
+ * stretch over 1 - rho (Section 3.3).  Computed on the host by Sturm-count
+ * bisection.  *steps (may be NULL) receives k.  LAP_ERR_UNSUPPORTED for
+ * LAP_PREC_PEGP_INNER (flexible CG has no Lanczos relation), LAP_ERR_INVALID_ARG
+ * before any solve, LAP_ERR_BREAKDOWN if a coefficient is not admissible.
+ */
+lap_status lap_estimate_condition(lap_handle h, int32_t *steps, double *lambda_min,
+                                  double *lambda_max);
 
 /* Same as lap_pcg_solve with host vectors: copies b in and x out on `stream`
  * (the copies are part of the call). */

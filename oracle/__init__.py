@@ -11,7 +11,7 @@ the paper (Hu & Lin, "Solving Graph Laplacians via Multilevel Sparsifiers"):
   sparsifier T (Section 3.3), each formed literally as sparse matrices;
 * ``oracle.solve``      -- the preconditioners z = P(mu) M P(mu)^T r with
   M = L_T^+ (MSP) or L_H^+ (PEGP, exact or by an inner iteration) and the outer
-  preconditioned conjugate gradient iteration.
+  preconditioned conjugate gradient iteration and flexible GMRES.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 leg of ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -24,5 +24,6 @@ without an independent pin say "parity unpinned" in their docstring.
 from .hierarchy import Hierarchy, build_hierarchy, splitmix64  # noqa: F401
 from .expanded import ExpandedOperators, expanded_operators, laplacian  # noqa: F401
 from .solve import (  # noqa: F401
-    OraclePreconditioner, make_preconditioner, pcg, SolveResult, solve,
+    OraclePreconditioner, fgmres, lanczos_extremes, make_preconditioner, pcg, SolveResult,
+    solve,
 )

@@ -145,6 +145,8 @@ class SolveResult:
     relres: float                    # true relative residual at exit
     history: list                    # recurrence relative residual after each iteration
     restarts: int = 0
+    alphas: list = field(default_factory=list)   # step lengths of the first CG run
+    betas: list = field(default_factory=list)    # direction coefficients of that run
 
 
 def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=False) -> SolveResult:
@@ -165,9 +167,12 @@ def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=Fals
     rho = r @ z
     its, restarts = 0, 0
     converged = False
+    alphas, betas = [], []
     while its < maxit:
         q = L @ p
         alpha = rho / (p @ q)
+        if restarts == 0:
+            alphas.append(alpha)
         x += alpha * p
         r_old = r
         r = r - alpha * q
@@ -188,17 +193,120 @@ def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=Fals
         z = M(r)
         rho_new = r @ z
         beta = (z @ (r - r_old)) / rho if flexible else rho_new / rho
+        if restarts == 0:
+            betas.append(beta)
         p = z + beta * p
         rho = rho_new
     x = _project(x)
     relres = np.linalg.norm(bp - L @ x) / nb
-    return SolveResult(x, its, converged, relres, hist, restarts)
+    return SolveResult(x, its, converged, relres, hist, restarts, alphas, betas[:len(alphas) - 1])
 
 
-def solve(g, b, kind="msp", *, mu=0.8, tol=1e-8, maxit=1000, **kw) -> SolveResult:
-    """Convenience: build the oracle preconditioner for graph g and run PCG."""
+def fgmres(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, restart=30) -> SolveResult:
+    """Flexible GMRES(m) with right preconditioning (Saad, SIAM J. Sci. Comput.
+    14, 1993), the outer Krylov method of the paper's experiments (Section 4),
+    on the singular consistent system L x = Pi b from x_0 = 0.
+
+    A cycle starts from the residual r (v_1 = r / ||r||).  Step j applies the
+    preconditioner, z_j = M(v_j), multiplies w = L z_j, orthogonalises w
+    against v_1..v_j by modified Gram-Schmidt (column j of the Hessenberg
+    matrix, h_(j+1,j) = ||w||, v_(j+1) = w / h_(j+1,j)), applies the earlier
+    Givens rotations to the column and a new one that zeroes h_(j+1,j); the
+    rotated right-hand side's entry j+1 is the residual norm of the least
+    squares solution, recorded relative to ||Pi b|| and tested against tol.
+    The cycle ends after `restart` steps or on convergence: y solves the
+    triangular system, x += Z y, and the next cycle starts from the true
+    residual Pi b - L x.  The iteration count is the number of products with
+    L inside the cycles; a cycle whose true residual meets tol ends the solve."""
+    L = sp.csr_matrix(L)
+    bp = _project(np.asarray(b, dtype=np.float64))
+    nb = np.linalg.norm(bp)
+    x = np.zeros_like(bp)
+    hist = []
+    if nb == 0.0:
+        return SolveResult(x, 0, True, 0.0, hist)
+    m = int(restart)
+    r = bp.copy()
+    its, cycles, converged = 0, 0, False
+    while its < maxit:
+        beta = np.linalg.norm(r)
+        if beta / nb <= tol:
+            converged = True
+            break
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            z = M(V[j])
+            Z.append(z)
+            w = L @ z
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            hn = np.linalg.norm(w)
+            H[j + 1, j] = hn
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j], H[j + 1, j] = d, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            rel = abs(g[j + 1]) / nb
+            hist.append(rel)
+            if rel <= tol or its >= maxit or hn == 0.0:
+                break
+            V.append(w / hn)
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        for i in range(k):
+            x += y[i] * Z[i]
+        cycles += 1
+        r = bp - L @ x
+        if np.linalg.norm(r) / nb <= tol:
+            converged = True
+            break
+    x = _project(x)
+    relres = np.linalg.norm(bp - L @ x) / nb
+    return SolveResult(x, its, converged, relres, hist, max(cycles - 1, 0))
+
+
+def lanczos_extremes(alphas, betas):
+    """Smallest and largest eigenvalue of the Lanczos tridiagonal T_k that CG's
+    coefficients define (Hestenes-Stiefel / Lanczos connection, e.g. Saad,
+    Iterative Methods for Sparse Linear Systems, Sec. 6.7.3):
+    T[j, j] = 1/alpha_j + beta_(j-1)/alpha_(j-1),  T[j, j+1] = sqrt(beta_j)/alpha_j.
+    Its eigenvalues (Ritz values) lie inside the spectrum of the preconditioned
+    operator and approach its extremes as k grows.  Dense eigensolve."""
+    a = np.asarray(alphas, dtype=np.float64)
+    b = np.asarray(betas, dtype=np.float64)[:len(a) - 1]
+    k = len(a)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / a[j] + (b[j - 1] / a[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(b[j]) / a[j]
+    ev = np.linalg.eigvalsh(T)
+    return ev[0], ev[-1]
+
+
+def solve(g, b, kind="msp", *, mu=0.8, tol=1e-8, maxit=1000, krylov="cg", restart=30,
+          **kw) -> SolveResult:
+    """Convenience: build the oracle preconditioner for graph g and run PCG
+    (krylov="cg") or FGMRES(restart) (krylov="fgmres")."""
     M = make_preconditioner(kind, g, mu=mu, **kw)
     L = M.ops.L if M.ops is not None else _laplacian_of(g)
+    if krylov == "fgmres":
+        return fgmres(L, b, M, tol=tol, maxit=maxit, restart=restart)
     return pcg(L, b, M, tol=tol, maxit=maxit, flexible=M.flexible)
 
 

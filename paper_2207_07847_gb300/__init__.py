@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblap.so")
 
 LAP_PREC = {"none": 0, "msp": 1, "pegp_inner": 2, "pegp_exact": 3}
 LAP_PRECISION = {"fp64": 0, "mixed": 1}
+LAP_KRYLOV = {"cg": 0, "fgmres": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not symmetric", 3: "not connected",
           4: "bad weight", 5: "out of memory", 6: "CUDA error", 7: "no convergence",
           8: "breakdown", 9: "timeout", 10: "cancelled", 11: "busy", 12: "unsupported"}
@@ -44,7 +45,8 @@ class lap_options(C.Structure):
                 ("refine_tol", C.c_double), ("max_refine", C.c_int32),
                 ("check_every", C.c_int32), ("timeout_s", C.c_double),
                 ("spmv_tpr", C.c_int32), ("host_only", C.c_int32),
-                ("stall_window", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("stall_window", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class lap_solve_info(C.Structure):
@@ -96,6 +98,8 @@ SIGNATURES = [
     ("lap_pegp_apply", _I32, [_VP, _VP, _VP, _VP]),
     ("lap_pcg_solve", _I32, [_VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_get_history", _I32, [_VP, _VP, _I32, C.POINTER(_I32)]),
+    ("lap_get_lanczos", _I32, [_VP, _VP, _VP, _I32, C.POINTER(_I32)]),
+    ("lap_estimate_condition", _I32, [_VP, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_D)]),
     ("lap_pcg_solve_host", _I32, [_VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_pcg_solve_batched", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_laplacian_residual_noalloc", _I32, [_I64, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -165,6 +169,8 @@ def make_options(**kw) -> lap_options:
             v = LAP_PREC[v]
         if k == "precision" and isinstance(v, str):
             v = LAP_PRECISION[v]
+        if k == "krylov" and isinstance(v, str):
+            v = LAP_KRYLOV[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
@@ -241,6 +247,10 @@ def lap_update_options(h: Handle, **opts):
     for k, v in opts.items():
         if k == "precision" and isinstance(v, str):
             v = LAP_PRECISION[v]
+        if k == "krylov" and isinstance(v, str):
+            v = LAP_KRYLOV[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
     _check(lib().lap_update_options(h, C.byref(o)), "lap_update_options")
     h.opts = o
@@ -248,7 +258,7 @@ def lap_update_options(h: Handle, **opts):
 
 
 KERNELS = {"spmv_L": 0, "spmv_LH": 1, "msp_sweep": 2, "update_up1": 3, "msp_tail": 4,
-           "band_down1": 5}
+           "band_down1": 5, "pegp_gemv": 6}
 
 
 def lap_kernel_bench(h: Handle, kernel, precision=0, reps=20):
@@ -322,6 +332,25 @@ def lap_get_history(h: Handle):
     out = np.empty(cnt.value, dtype=np.float64)
     _check(lib().lap_get_history(h, out.ctypes.data, cnt.value, C.byref(cnt)), "lap_get_history")
     return out[:cnt.value]
+
+
+def lap_get_lanczos(h: Handle):
+    """(alpha, beta) of the last solve's first CG run (numpy arrays)."""
+    cnt = C.c_int32()
+    _check(lib().lap_get_lanczos(h, None, None, 0, C.byref(cnt)), "lap_get_lanczos")
+    a = np.empty(cnt.value, dtype=np.float64)
+    b = np.empty(cnt.value, dtype=np.float64)
+    _check(lib().lap_get_lanczos(h, a.ctypes.data, b.ctypes.data, cnt.value, C.byref(cnt)),
+           "lap_get_lanczos")
+    return a[:cnt.value], b[:cnt.value]
+
+
+def lap_estimate_condition(h: Handle):
+    """(steps, lambda_min, lambda_max) of B L from the last solve's CG run."""
+    k, lo, hi = C.c_int32(), C.c_double(), C.c_double()
+    _check(lib().lap_estimate_condition(h, C.byref(k), C.byref(lo), C.byref(hi)),
+           "lap_estimate_condition")
+    return k.value, lo.value, hi.value
 
 
 def lap_pcg_solve_host(h: Handle, b, x, stream=None) -> lap_solve_info:

@@ -546,14 +546,7 @@ k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V
     double v[3] = {sz, srz, szq};
     if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
         const double m = v[0] / (double)n;
-        const double rho_new = v[1] - m * sc->rs;
-        sc->zmean = m;
-        if (sc->first) sc->beta = 0.0;
-        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
-        else sc->beta = rho_new / sc->rho;
-        sc->rho = rho_new;
-        sc->first = 0;
-        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+        set_direction(sc, m, v[1] - m * sc->rs, v[2]);
     }
 }
 

@@ -18,9 +18,12 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <type_traits>
 
+#include "dense.cuh"
+#include "fgmres.cuh"
 #include "kernels.cuh"
 #include "solver.cuh"
 
@@ -780,6 +783,7 @@ template <> struct Sel<double> {
     static const DevMsp<double> &M(const lap_handle_s &h) { return h.M64; }
     static const CgVectors<double> &w(const lap_handle_s &h) { return h.w64; }
     static const CgVectors<double> &e(const lap_handle_s &h) { return h.e64; }
+    static const double *G(const lap_handle_s &h) { return h.G64; }
     static const CgState &st(const lap_handle_s &h) { return h.st64; }
     static const CgState &ste(const lap_handle_s &h) { return h.ste64; }
     static cudaGraphExec_t &gi(lap_handle_s &h) { return h.g_iter64; }
@@ -793,6 +797,7 @@ template <> struct Sel<float> {
     static const DevMsp<float> &M(const lap_handle_s &h) { return h.M32; }
     static const CgVectors<float> &w(const lap_handle_s &h) { return h.w32; }
     static const CgVectors<float> &e(const lap_handle_s &h) { return h.e32; }
+    static const float *G(const lap_handle_s &h) { return h.G32; }
     static const CgState &st(const lap_handle_s &h) { return h.st32; }
     static const CgState &ste(const lap_handle_s &h) { return h.ste32; }
     static cudaGraphExec_t &gi(lap_handle_s &h) { return h.g_iter32; }
@@ -803,6 +808,33 @@ template <> struct Sel<float> {
 
 bool is_plain(const lap_handle_s &h) { return h.m.opt.prec == LAP_PREC_NONE; }
 bool is_pegp(const lap_handle_s &h) { return h.m.opt.prec == LAP_PREC_PEGP_INNER; }
+// exact PEGP with at least two levels (one level: H = T = G, the MSP path)
+bool is_exact(const lap_handle_s &h) { return h.m.opt.prec == LAP_PREC_PEGP_EXACT && h.G64; }
+
+// Exact PEGP (Section 3.2, M = L_H^+): z = Pi P(mu) G P(mu)^T r with the dense
+// G applied between the restriction and the prolongation; UPDATE first takes
+// the CG step x += alpha p, r -= alpha q.  Every kernel checks the device
+// flag, so the sequence can be captured in a graph.
+template <typename V>
+void precond_exact(const lap_handle_s &h, bool update, cudaStream_t s)
+{
+    const auto &w = Sel<V>::w(h);
+    const auto &st = Sel<V>::st(h);
+    const auto &M = Sel<V>::M(h);
+    const auto &e = Sel<V>::e(h);
+    const int64_t n = M.off[1], nt = M.off[M.levels];
+    if (update) {
+        h.launches += 1;
+        k_update<V, true, false><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), w.x, w.r, w.p,
+                                                                   w.q, nullptr, st.sc, st.part,
+                                                                   st.ticket);
+    }
+    restrict_tilde<V>(h, M, w.r, e.r, nullptr, e.T, st.sc, s);
+    h.launches += 1;
+    k_dense_gemv<V><<<grid_for(h, nt * 32), kBlock, 0, s>>>(static_cast<int>(nt), h.g_ld, Sel<V>::G(h),
+                                                          e.r, e.x, st.sc);
+    prolong_tilde_to_z<V>(h, M, e.x, e.T, w, st, s);
+}
 
 // one outer CG iteration for the graph-captured preconditioners (MSP, none)
 template <typename V>
@@ -811,7 +843,8 @@ void outer_iteration(const lap_handle_s &h, cudaStream_t s)
     const auto &w = Sel<V>::w(h);
     const auto &st = Sel<V>::st(h);
     spmv<V, 0>(h, Sel<V>::L(h), h.tpr, w.p, w.q, nullptr, nullptr, st, s);
-    precond_msp<V>(h, Sel<V>::M(h), w, st, true, is_plain(h), s);
+    if (is_exact(h)) precond_exact<V>(h, true, s);
+    else precond_msp<V>(h, Sel<V>::M(h), w, st, true, is_plain(h), s);
     pupdate<V>(h, Sel<V>::M(h).off[1], is_plain(h) ? w.r : w.z, w.p, st, s);
 }
 
@@ -865,6 +898,10 @@ lap_status apply_precond(lap_handle_s &h, bool update, Clock::time_point t0, int
     const auto &st = Sel<V>::st(h);
     const auto &M = Sel<V>::M(h);
     const int64_t n = M.off[1];
+    if (is_exact(h)) {
+        precond_exact<V>(h, update, s);
+        return LAP_OK;
+    }
     if (!is_pegp(h) || M.levels == 1) {
         // one level: H = T = G, so the dense top-level solve is PEGP exactly
         precond_msp<V>(h, M, w, st, update, is_plain(h), s);
@@ -966,7 +1003,7 @@ lap_status cg_fp64(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
     const auto &st = h.st64;
     const int64_t n = h.M64.off[1];
     const lap_options &o = h.m.opt;
-    k_cg_reset<<<1, 1, 0, s>>>(st.sc, o.tol, o.maxit, is_pegp(h) ? 1 : 0, h.hist, o.maxit);
+    k_cg_reset<<<1, 1, 0, s>>>(st.sc, o.tol, o.maxit, is_pegp(h) ? 1 : 0, h.hist, o.maxit, h.lz);
     h.launches += 2;
     k_center_init<double><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), h.bs, w.r, w.x, st.sc,
                                                             st.part, st.ticket);
@@ -982,6 +1019,7 @@ lap_status cg_fp64(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
     lap_status result = LAP_ERR_NO_CONVERGENCE;
     for (;;) {
         lap_status it = iterate<double>(h, t0, inner, sc);
+        if (h.lz_run < 0) h.lz_run = sc.iter;     // the first run ends here
         if (it != LAP_OK) {
             result = it;
             break;
@@ -1062,7 +1100,7 @@ lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
         }
         const double tol_in = std::min(0.5, std::max(o.refine_tol, 0.3 * o.tol / relres));
         k_cg_reset<<<1, 1, 0, s>>>(si.sc, tol_in, o.maxit - total, is_pegp(h) ? 1 : 0, h.hist + total,
-                                   o.maxit - total);
+                                   o.maxit - total, h.lz + 2 * total);
         h.launches += 5;
         k_gather_sum<float><<<grid_for(h, n), kBlock, 0, s>>>(ni, nullptr, h.w64.r, h.w32.r, si.sc,
                                                              si.part, si.ticket);
@@ -1072,6 +1110,7 @@ lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
         pupdate<float>(h, n, is_plain(h) ? h.w32.r : h.w32.z, h.w32.p, si, s);
         CgScalars sci;
         lap_status it = iterate<float>(h, t0, inner, sci);
+        if (h.lz_run < 0) h.lz_run = sci.iter;    // the first inner solve
         if (it != LAP_OK) {
             result = it;
             break;
@@ -1093,6 +1132,143 @@ lap_status cg_mixed(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
     info.iterations = total;
     info.inner_iterations = inner;
     info.relres = relres;
+    return result;
+}
+
+// ---------------------------------------------------------------------------
+// Flexible GMRES(m) in FP64 (fgmres.cuh): the cycle's kernels check the device
+// flag, so for the preconditioners without host polling (MSP, exact PEGP,
+// none) a whole cycle is captured once as a CUDA graph and replayed; the
+// PEGP inner solve polls the host and runs the cycle's launches directly.
+template <typename T>
+T *member(GmState *gm, size_t off)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(gm) + off);
+}
+
+lap_status gm_alloc(lap_handle_s &h, int m)
+{
+    if (h.gm_V && h.gm_m == m) return LAP_OK;
+    const size_t n = static_cast<size_t>(h.M64.off[1]);
+    h.gm_V = dalloc<double>(h, n * (m + 1));
+    h.gm_Z = dalloc<double>(h, n * m);
+    h.gm_part = dalloc<double>(h, static_cast<size_t>(m + 1) * kGmDotBlocks);
+    h.gm = dalloc<GmState>(h, 1);
+    if (!h.gm_V || !h.gm_Z || !h.gm_part || !h.gm) return LAP_ERR_OOM;
+    h.gm_m = m;
+    if (h.g_gm) {
+        cudaGraphExecDestroy(h.g_gm);
+        h.g_gm = nullptr;
+    }
+    return LAP_OK;
+}
+
+// step j of the cycle: z_j = B v_j, w = L z_j, two Gram-Schmidt passes,
+// v_(j+1), the Givens update
+lap_status gm_step(lap_handle_s &h, int j, Clock::time_point t0, int &inner)
+{
+    const cudaStream_t s = h.s;
+    const auto &w = h.w64;
+    const auto &st = h.st64;
+    const int n = static_cast<int>(h.M64.off[1]);
+    double *Vj = h.gm_V + static_cast<int64_t>(j) * n;
+    double *Zj = h.gm_Z + static_cast<int64_t>(j) * n;
+    double *Vn = Vj + n;
+    const int gn = grid_for(h, n);
+    if (is_plain(h)) {
+        h.launches += 1;
+        k_gm_store_z<<<gn, kBlock, 0, s>>>(n, Vj, nullptr, Zj, st.sc);
+    } else {
+        h.launches += 2;
+        k_copy2<double><<<gn, kBlock, 0, s>>>(n, Vj, w.r, nullptr, st.sc);
+        LAP_TRY(apply_precond<double>(h, false, t0, inner));
+        k_gm_store_z<<<gn, kBlock, 0, s>>>(n, w.z, &st.sc->zmean, Zj, st.sc);
+    }
+    // MODE 0 stops with the flag (its CG scalars are not used here)
+    spmv<double, 0>(h, h.L64, h.tpr, Zj, w.q, nullptr, nullptr, st, s);
+    const int nc = j + 1;
+    const int nbx = std::max(1, std::min(kGmDotBlocks, (n + kBlock - 1) / kBlock));
+    double *h1 = member<double>(h.gm, offsetof(GmState, h1));
+    double *h2 = member<double>(h.gm, offsetof(GmState, h2));
+    for (double *hc : {h1, h2}) {
+        k_gm_dots<<<dim3(nbx, nc), kBlock, 0, s>>>(n, h.gm_V, w.q, h.gm_part, st.sc);
+        k_gm_dots_sum<<<nc, kBlock, 0, s>>>(nbx, h.gm_part, hc, st.sc);
+        k_gm_orth<<<gn, kBlock, 0, s>>>(n, nc, h.gm_V, hc, w.q, h.gm, st.sc, st.part, st.ticket);
+    }
+    k_gm_scale<<<gn, kBlock, 0, s>>>(n, w.q, Vn, h.gm, st.sc);
+    k_gm_givens<<<1, 1, 0, s>>>(j, h.gm, st.sc);
+    h.launches += 8;
+    return LAP_OK;
+}
+
+// one cycle from the residual in w.r: start, m steps, y and x += Z y, then
+// the true residual r = Pi b - L x (into w.r, ||r|| into the scalars)
+lap_status gm_cycle(lap_handle_s &h, Clock::time_point t0, int &inner)
+{
+    const cudaStream_t s = h.s;
+    const auto &w = h.w64;
+    const auto &st = h.st64;
+    const int n = static_cast<int>(h.M64.off[1]);
+    const int gn = grid_for(h, n);
+    h.launches += 3;
+    k_gm_start<<<gn, kBlock, 0, s>>>(n, w.r, h.gm_V, st.sc, h.gm);
+    for (int j = 0; j < h.gm_m; ++j) LAP_TRY(gm_step(h, j, t0, inner));
+    k_gm_solve<<<1, 1, 0, s>>>(h.gm, st.sc);
+    k_gm_xupdate<<<gn, kBlock, 0, s>>>(n, h.gm_Z, h.gm, w.x);
+    spmv<double, 1>(h, h.L64, h.tpr, w.x, nullptr, h.bs, w.r, st, s);
+    return LAP_OK;
+}
+
+lap_status fgmres_fp64(lap_handle_s &h, Clock::time_point t0, lap_solve_info &info)
+{
+    const cudaStream_t s = h.s;
+    const auto &w = h.w64;
+    const auto &st = h.st64;
+    const int64_t n = h.M64.off[1];
+    const lap_options &o = h.m.opt;
+    LAP_TRY(gm_alloc(h, o.restart));
+    k_cg_reset<<<1, 1, 0, s>>>(st.sc, o.tol, o.maxit, 0, h.hist, o.maxit, nullptr);
+    h.launches += 2;
+    k_center_init<double><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), h.bs, w.r, w.x, st.sc,
+                                                            st.part, st.ticket);
+    CgScalars sc;
+    LAP_TRY(poll(h, st, sc));
+    if (!(sc.bnorm > 0.0)) {
+        info.relres = 0.0;
+        return LAP_OK;
+    }
+    const bool graph = !is_pegp(h);
+    int inner = 0, cycles = 0;
+    lap_status result = LAP_ERR_NO_CONVERGENCE;
+    for (;;) {
+        if (graph) {
+            if (!h.g_gm) LAP_TRY(capture(h, h.g_gm, h.nodes_gm, [&] { (void)gm_cycle(h, t0, inner); }));
+            LAP_CK(cudaGraphLaunch(h.g_gm, s));
+            h.launches += h.nodes_gm;
+        } else {
+            LAP_TRY(gm_cycle(h, t0, inner));
+        }
+        LAP_TRY(poll(h, st, sc));
+        ++cycles;
+        if (sc.relres <= o.tol) {
+            result = LAP_OK;
+            break;
+        }
+        if (sc.stop == kBreakdown) {
+            result = LAP_ERR_BREAKDOWN;
+            break;
+        }
+        if (sc.iter >= o.maxit) break;
+        if (timed_out(h, t0)) {
+            result = LAP_ERR_TIMEOUT;
+            break;
+        }
+    }
+    info.iterations = sc.iter;
+    info.restarts = cycles - 1;
+    info.inner_iterations = inner;
+    info.relres = sc.relres;
+    info.relres_recurrence = sc.relres;
     return result;
 }
 
@@ -1121,8 +1297,14 @@ lap_status solve_core(lap_handle_s &h, const double *b, double *x, lap_solve_inf
     k_gather_sum<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.perm1, b, h.bs, h.st64.sc, h.st64.part,
                                                           h.st64.ticket);
     h.launches += 3;   // gather, mean, scatter
-    lap_status st = h.m.opt.precision == LAP_MIXED ? cg_mixed(h, t0, info) : cg_fp64(h, t0, info);
+    h.lz_run = -1;
+    lap_status st;
+    if (h.m.opt.krylov == LAP_KRYLOV_FGMRES)
+        st = h.m.opt.precision == LAP_MIXED ? LAP_ERR_UNSUPPORTED : fgmres_fp64(h, t0, info);
+    else
+        st = h.m.opt.precision == LAP_MIXED ? cg_mixed(h, t0, info) : cg_fp64(h, t0, info);
     h.hist_count = std::min(info.iterations, h.m.opt.maxit);
+    h.lz_run = std::min(std::max(h.lz_run, 0), h.hist_count);
     // x = Pi x back in the caller's numbering (also for a non-converged result)
     k_mean<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.w64.x, h.stb.sc, h.stb.part, h.stb.ticket);
     k_scatter_shift<double><<<grid_for(h, n), kBlock, 0, s>>>(n, h.perm1, h.w64.x, x,
@@ -1130,6 +1312,70 @@ lap_status solve_core(lap_handle_s &h, const double *b, double *x, lap_solve_inf
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return LAP_ERR_CUDA;
     return st;
+}
+
+// Exact PEGP: G = S (S L_H S + v v^T / v^T v)^-1 S (see dense.cuh), inverted
+// on the device by blocked Gauss-Jordan, with an FP32 copy for mixed
+// precision.  Expanded sizes above kDenseMaxN are not inverted densely.
+lap_status upload_dense_pegp(lap_handle_s &h, bool mixed)
+{
+    const HostCsr &H = h.m.LH;
+    if (H.n > kDenseMaxN) return LAP_ERR_UNSUPPORTED;
+    const int nt = static_cast<int>(H.n);
+    const int np = (nt + kGjB - 1) / kGjB * kGjB;
+    std::vector<double> sv(static_cast<size_t>(nt)), vv(static_cast<size_t>(nt));
+    double vtv = 0.0;
+    for (int i = 0; i < nt; ++i) {
+        const double d = H.diag[i];
+        if (!(d > 0.0) || !std::isfinite(d)) return LAP_ERR_BREAKDOWN;
+        vv[i] = std::sqrt(d);
+        sv[i] = 1.0 / vv[i];
+        vtv += d;
+    }
+    const size_t nn = static_cast<size_t>(np) * np;
+    h.G64 = dalloc<double>(h, nn);
+    if (!h.G64) return LAP_ERR_OOM;
+    if (mixed) {
+        h.G32 = dalloc<float>(h, nn);
+        if (!h.G32) return LAP_ERR_OOM;
+    }
+    h.g_ld = np;
+    // set-up scratch, released on return
+    DevBuf brp, bci, bw, bs, bv, bB, bC, bR, bbad;
+    if (!brp.alloc(sizeof(int64_t) * (nt + 1)) || !bci.alloc(sizeof(int) * std::max<size_t>(H.ci.size(), 1)) ||
+        !bw.alloc(sizeof(double) * std::max<size_t>(H.w.size(), 1)) || !bs.alloc(sizeof(double) * nt) ||
+        !bv.alloc(sizeof(double) * nt) || !bB.alloc(sizeof(double) * kGjB * kGjB) ||
+        !bC.alloc(sizeof(double) * static_cast<size_t>(np) * kGjB) ||
+        !bR.alloc(sizeof(double) * static_cast<size_t>(np) * kGjB) || !bbad.alloc(sizeof(int)))
+        return LAP_ERR_OOM;
+    const cudaStream_t s = h.s;
+    LAP_CK(cudaMemcpyAsync(brp.p, H.rp.data(), sizeof(int64_t) * (nt + 1), cudaMemcpyHostToDevice, s));
+    if (!H.ci.empty()) {
+        LAP_CK(cudaMemcpyAsync(bci.p, H.ci.data(), sizeof(int) * H.ci.size(), cudaMemcpyHostToDevice, s));
+        LAP_CK(cudaMemcpyAsync(bw.p, H.w.data(), sizeof(double) * H.w.size(), cudaMemcpyHostToDevice, s));
+    }
+    LAP_CK(cudaMemcpyAsync(bs.p, sv.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
+    LAP_CK(cudaMemcpyAsync(bv.p, vv.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, s));
+    LAP_CK(cudaMemsetAsync(bbad.p, 0, sizeof(int), s));
+    const int gfill = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(nn) + kBlock - 1) / kBlock,
+                                                         int64_t(h.sms) * 16));
+    k_dense_fill<<<gfill, kBlock, 0, s>>>(np, nt, bv.as<double>(), 1.0 / vtv, h.G64);
+    k_dense_scatter<<<grid_for(h, nt), kBlock, 0, s>>>(nt, np, brp.as<int64_t>(), bci.as<int>(),
+                                                       bw.as<double>(), bs.as<double>(), h.G64);
+    const int tiles = np / kGjB;
+    for (int t = 0; t < tiles; ++t) {
+        const int k0 = t * kGjB;
+        k_gj_pivot<<<1, kGjThreads, 0, s>>>(np, k0, h.G64, bB.as<double>(), bbad.as<int>());
+        k_gj_panels<<<tiles, kGjThreads, 0, s>>>(np, k0, h.G64, bB.as<double>(), bC.as<double>(),
+                                                  bR.as<double>());
+        k_gj_update<<<dim3(tiles, tiles), kGjThreads, 0, s>>>(np, k0, h.G64, bB.as<double>(),
+                                                             bC.as<double>(), bR.as<double>());
+    }
+    k_dense_finish<<<gfill, kBlock, 0, s>>>(np, nt, bs.as<double>(), h.G64, h.G32);
+    int bad = 0;
+    LAP_CK(cudaMemcpyAsync(&bad, bbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LAP_CK(cudaStreamSynchronize(s));
+    return bad ? LAP_ERR_BREAKDOWN : LAP_OK;
 }
 
 }  // namespace
@@ -1162,6 +1408,7 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
         make_sell(m.LH, sl, 0);
         LAP_TRY(upload_csr<double>(h, m.LH, sl, h.H64, nullptr));
         if (mixed) LAP_TRY(upload_csr<float>(h, m.LH, sl, h.H32, &h.H64));
+        if (m.opt.prec == LAP_PREC_PEGP_EXACT && m.levels > 1) LAP_TRY(upload_dense_pegp(h, mixed));
     }
     LAP_TRY(upload(h, &h.perm1, m.lev[0].perm));
     {
@@ -1185,7 +1432,8 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
     LAP_TRY(alloc_state(h, h.stb));
     h.hist_capacity = std::max(m.opt.maxit, 1000);
     h.hist = dalloc<double>(h, static_cast<size_t>(h.hist_capacity));
-    if (!h.hist) return LAP_ERR_OOM;
+    h.lz = dalloc<double>(h, 2 * static_cast<size_t>(h.hist_capacity));
+    if (!h.hist || !h.lz) return LAP_ERR_OOM;
     // matvec kernel choice: the option forces one, 0 times the candidates
     h.tpr = 0;
     h.tprH = 0;
@@ -1203,7 +1451,7 @@ void destroy_handle(lap_handle_s &h)
 {
     if (h.s) cudaStreamSynchronize(h.s);
     h.batch.reset();
-    for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32})
+    for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32, &h.g_gm})
         if (*g) {
             cudaGraphExecDestroy(*g);
             *g = nullptr;
@@ -1338,6 +1586,21 @@ lap_status get_history(lap_handle_s &h, double *out, int cap, int *count)
     return LAP_OK;
 }
 
+lap_status get_lanczos(lap_handle_s &h, double *alpha, double *beta, int cap, int *count)
+{
+    const int c = std::min(h.lz_run, h.hist_capacity);
+    *count = c;
+    if (cap <= 0 || c == 0) return LAP_OK;
+    const int m = std::min(c, cap);
+    std::vector<double> ab(2 * static_cast<size_t>(m));
+    LAP_CK(cudaMemcpy(ab.data(), h.lz, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < m; ++j) {
+        if (alpha) alpha[j] = ab[2 * j];
+        if (beta) beta[j] = j + 1 < c ? ab[2 * j + 1] : 0.0;   // the last step has no successor
+    }
+    return LAP_OK;
+}
+
 lap_status update_options(lap_handle_s &h, const lap_options &o)
 {
     if (!(o.tol > 0.0) || o.maxit < 1 || o.check_every < 1 || o.inner_maxit < 1 ||
@@ -1345,13 +1608,18 @@ lap_status update_options(lap_handle_s &h, const lap_options &o)
         return LAP_ERR_INVALID_ARG;
     if (o.precision != LAP_FP64 && o.precision != LAP_MIXED) return LAP_ERR_INVALID_ARG;
     if (o.precision == LAP_MIXED && !h.L32.w) return LAP_ERR_INVALID_ARG;
+    if (o.krylov != LAP_KRYLOV_CG && o.krylov != LAP_KRYLOV_FGMRES) return LAP_ERR_INVALID_ARG;
+    if (o.restart < 1 || o.restart > kGmMax) return LAP_ERR_INVALID_ARG;
     if (h.host_only) return LAP_ERR_INVALID_ARG;
     lap_options &cur = h.m.opt;
     if (o.maxit > h.hist_capacity) {
         double *p = dalloc<double>(h, static_cast<size_t>(o.maxit));
-        if (!p) return LAP_ERR_OOM;
+        double *q = dalloc<double>(h, 2 * static_cast<size_t>(o.maxit));
+        if (!p || !q) return LAP_ERR_OOM;
         h.hist = p;
+        h.lz = q;
         h.hist_capacity = o.maxit;
+        h.hist_count = h.lz_run = 0;
     }
     if (o.check_every != cur.check_every) {
         for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32})
@@ -1370,6 +1638,8 @@ lap_status update_options(lap_handle_s &h, const lap_options &o)
     cur.timeout_s = o.timeout_s;
     cur.precision = o.precision;
     cur.stall_window = o.stall_window;
+    cur.krylov = o.krylov;
+    cur.restart = o.restart;
     return LAP_OK;
 }
 
@@ -1416,7 +1686,8 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
 {
     if (precision == 1 && !h.L32.w) return LAP_ERR_INVALID_ARG;
     if (kernel == 1 && !h.H64.w) return LAP_ERR_INVALID_ARG;
-    if (kernel < 0 || kernel > 5) return LAP_ERR_INVALID_ARG;
+    if (kernel == 6 && !h.G64) return LAP_ERR_INVALID_ARG;
+    if (kernel < 0 || kernel > 6) return LAP_ERR_INVALID_ARG;
     const cudaStream_t s = h.s;
     cudaEvent_t e0, e1;
     LAP_CK(cudaEventCreate(&e0));
@@ -1448,6 +1719,12 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
                 k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, h.stb.sc);
                 break;
             }
+            case 6: {
+                const int64_t nt = M.off[M.levels];
+                k_dense_gemv<V><<<grid_for(h, nt * 32), kBlock, 0, s>>>(
+                    static_cast<int>(nt), h.g_ld, Sel<V>::G(h), Sel<V>::e(h).r, Sel<V>::e(h).x, h.stb.sc);
+                break;
+            }
             default: {
                 const BandParams<V> &P = M.band_n[0];
                 k_band_down<V, true, false><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
@@ -1475,6 +1752,10 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
                 const double nk = M.lev[k].n, na = M.lev[k].nagg;
                 by += 4.0 * (na + 1) + sv * (4 * na + 3 * (nk - 2 * na));
             }
+        } else if (kernel == 6) {
+            // exact PEGP matvec: G (ntilde^2) and r~ read, y~ written
+            const double nt = static_cast<double>(M.off[M.levels]);
+            by = sv * nt * nt + 2.0 * sv * nt;
         } else {
             if (M.band_n.empty()) return -1.0;
             // first band down: deltas and segments of its levels read, the

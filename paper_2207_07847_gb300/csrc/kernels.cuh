@@ -46,9 +46,44 @@ struct CgScalars {
     int first;         // 1 while preparing the initial direction
     int hist_cap;      // capacity of hist
     double *hist;      // optional recurrence-residual history (device), or null
+    double *lz;        // optional (alpha, beta) of every step, 2 * hist_cap, or null
+    int stop;          // FGMRES: the flag that ended the latest cycle
 };
 
 enum : int { kRun = 0, kConverged = 1, kBreakdown = 2, kMaxit = 3 };
+
+// A completed step (x += alpha p, r -= alpha q, rr = ||r||^2): count it,
+// record its recurrence residual and alpha, test convergence.
+__device__ __forceinline__ void finish_step(CgScalars *sc, double rr)
+{
+    sc->iter += 1;
+    const double rel = sqrt(rr) / sc->bnorm;
+    sc->relres = rel;
+    if (sc->iter <= sc->hist_cap) {
+        sc->hist[sc->iter - 1] = rel;
+        if (sc->lz) sc->lz[2 * (sc->iter - 1)] = sc->alpha;
+    }
+    if (!isfinite(rel)) sc->flag = kBreakdown;
+    else if (rel <= sc->tol) sc->flag = kConverged;
+    else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+}
+
+// Next direction's coefficients from z = B r: m = mean(z), rho_new = r^T Pi z,
+// zq = z^T q (flexible CG only).  beta = rho_new / rho, or Notay's FCG(1)
+// choice -alpha (Pi z)^T q / rho when the preconditioner varies; recorded
+// beside the step's alpha (the pairs define CG's Lanczos tridiagonal).
+__device__ __forceinline__ void set_direction(CgScalars *sc, double m, double rho_new, double zq)
+{
+    sc->zmean = m;
+    if (sc->first) sc->beta = 0.0;
+    else if (sc->flexible) sc->beta = -sc->alpha * (zq - m * sc->qsum) / sc->rho;
+    else sc->beta = rho_new / sc->rho;
+    if (!sc->first && sc->lz && sc->iter >= 1 && sc->iter <= sc->hist_cap)
+        sc->lz[2 * (sc->iter - 1) + 1] = sc->beta;
+    sc->rho = rho_new;
+    sc->first = 0;
+    if (!isfinite(rho_new)) sc->flag = kBreakdown;
+}
 
 // ---------------------------------------------------------------------------
 // Deterministic grid reduction: every block reduces its NV partial sums, the
@@ -380,22 +415,12 @@ k_update(int n, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
         sc->rr = v[0];
         sc->rs = v[1];
         if (UPDATE) {
-            sc->iter += 1;
-            const double rel = sqrt(v[0]) / sc->bnorm;
-            sc->relres = rel;
-            if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
-            if (!isfinite(rel)) sc->flag = kBreakdown;
-            else if (rel <= sc->tol) sc->flag = kConverged;
-            else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+            finish_step(sc, v[0]);
         }
         if (PLAIN) {
             // unpreconditioned CG: z = Pi r
             const double m = v[1] / (double)n;
-            const double rho_new = v[0] - m * v[1];
-            sc->zmean = m;
-            sc->beta = sc->first ? 0.0 : rho_new / sc->rho;
-            sc->rho = rho_new;
-            sc->first = 0;
+            set_direction(sc, m, v[0] - m * v[1], 0.0);
         }
     }
 }
@@ -627,13 +652,7 @@ k_up_tiled(int nagg, const int *__restrict__ seg, const V *__restrict__ inv,
         sc->rr = v[0];
         sc->rs = v[1];
         if (MODE == 1) {
-            sc->iter += 1;
-            const double rel = sqrt(v[0]) / sc->bnorm;
-            sc->relres = rel;
-            if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
-            if (!isfinite(rel)) sc->flag = kBreakdown;
-            else if (rel <= sc->tol) sc->flag = kConverged;
-            else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+            finish_step(sc, v[0]);
         }
     }
 }
@@ -700,14 +719,7 @@ k_down_tiled(int n, int nagg, const int *__restrict__ seg, const V *__restrict__
     double v[3] = {sz, srz, szq};
     if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
         const double m = v[0] / (double)n;
-        const double rho_new = v[1] - m * sc->rs;
-        sc->zmean = m;
-        if (sc->first) sc->beta = 0.0;
-        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
-        else sc->beta = rho_new / sc->rho;
-        sc->rho = rho_new;
-        sc->first = 0;
-        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+        set_direction(sc, m, v[1] - m * sc->rs, v[2]);
     }
 }
 
@@ -777,13 +789,7 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
             sc->rr = v[0];
             sc->rs = v[1];
             if (P.fin == 1) {
-                sc->iter += 1;
-                const double rel = sqrt(v[0]) / sc->bnorm;
-                sc->relres = rel;
-                if (sc->hist && sc->iter <= sc->hist_cap) sc->hist[sc->iter - 1] = rel;
-                if (!isfinite(rel)) sc->flag = kBreakdown;
-                else if (rel <= sc->tol) sc->flag = kConverged;
-                else if (sc->iter >= sc->maxit) sc->flag = kMaxit;
+                finish_step(sc, v[0]);
             }
             stop = sc->flag != kRun;
         }
@@ -929,14 +935,7 @@ k_dense_z(int n, const double *__restrict__ G, const V *__restrict__ r, const V 
     double v[3] = {sz, srz, szq};
     if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
         const double m = v[0] / (double)n;
-        const double rho_new = v[1] - m * sc->rs;
-        sc->zmean = m;
-        if (sc->first) sc->beta = 0.0;
-        else if (sc->flexible) sc->beta = -sc->alpha * (v[2] - m * sc->qsum) / sc->rho;
-        else sc->beta = rho_new / sc->rho;
-        sc->rho = rho_new;
-        sc->first = 0;
-        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+        set_direction(sc, m, v[1] - m * sc->rs, v[2]);
     }
 }
 
@@ -1079,18 +1078,13 @@ k_zred(int64_t n, const V *__restrict__ z, const V *__restrict__ r, CgScalars *s
     double v[2] = {sz, srz};
     if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
         const double m = v[0] / (double)n;
-        const double rho_new = v[1] - m * sc->rs;
-        sc->zmean = m;
-        sc->beta = sc->first ? 0.0 : rho_new / sc->rho;
-        sc->rho = rho_new;
-        sc->first = 0;
-        if (!isfinite(rho_new)) sc->flag = kBreakdown;
+        set_direction(sc, m, v[1] - m * sc->rs, 0.0);
     }
 }
 
 // CG bookkeeping written from the host side of the stream.
 static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flexible, double *hist,
-                                  int hist_cap)
+                                  int hist_cap, double *lz = nullptr)
 {
     sc->tol = tol;
     sc->maxit = maxit;
@@ -1100,6 +1094,7 @@ static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flex
     sc->first = 1;
     sc->hist = hist;
     sc->hist_cap = hist ? hist_cap : 0;
+    sc->lz = hist ? lz : nullptr;
 }
 
 // scalars for timing runs: running, never converging, unit norms
@@ -1118,6 +1113,7 @@ static __global__ void k_bench_scalars(CgScalars *sc)
     sc->zmean = 0.0;
     sc->hist = nullptr;
     sc->hist_cap = 0;
+    sc->lz = nullptr;
 }
 
 static __global__ void k_cg_restart(CgScalars *sc)

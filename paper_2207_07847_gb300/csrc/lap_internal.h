@@ -135,4 +135,14 @@ uint64_t splitmix64(uint64_t seed, uint64_t i);
 void *dev_alloc(size_t bytes, void *stream);
 void dev_free(void *p, void *stream);
 
+// Tridiagonal (a, b) of CG's Lanczos process from its first k step lengths
+// alpha and coefficients beta: a_j = 1/alpha_j + beta_(j-1)/alpha_(j-1),
+// b_j = sqrt(beta_j)/alpha_j.  False if a coefficient is not admissible
+// (alpha <= 0, beta < 0, or not finite).
+bool lanczos_tridiagonal(const double *alpha, const double *beta, int k, std::vector<double> &a,
+                         std::vector<double> &b);
+// Smallest and largest eigenvalue of the symmetric tridiagonal matrix with
+// diagonal a and off-diagonal b, by Sturm-count bisection.
+bool tridiag_extremes(const std::vector<double> &a, const std::vector<double> &b, double *lo, double *hi);
+
 }  // namespace lap

@@ -92,6 +92,8 @@ void lap_options_default(lap_options *o)
     o->spmv_tpr = 0;
     o->host_only = 0;
     o->stall_window = 1000;
+    o->krylov = LAP_KRYLOV_CG;
+    o->restart = 30;
 }
 
 const char *lap_status_string(int32_t s)
@@ -135,7 +137,8 @@ lap_status lap_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     if (o.prec < LAP_PREC_NONE || o.prec > LAP_PREC_PEGP_EXACT) return LAP_ERR_INVALID_ARG;
     if (o.precision != LAP_FP64 && o.precision != LAP_MIXED) return LAP_ERR_INVALID_ARG;
     if (!(o.tol > 0.0) || o.maxit < 1 || o.check_every < 1) return LAP_ERR_INVALID_ARG;
-    if (o.prec == LAP_PREC_PEGP_EXACT) return LAP_ERR_UNSUPPORTED;
+    if (o.krylov != LAP_KRYLOV_CG && o.krylov != LAP_KRYLOV_FGMRES) return LAP_ERR_INVALID_ARG;
+    if (o.restart < 1 || o.restart > 128) return LAP_ERR_INVALID_ARG;
     std::string why;
     lap_status st = validate_csr(n, row_ptr, col_idx, w, &why);
     if (st != LAP_OK) return st;
@@ -186,6 +189,33 @@ lap_status lap_get_history(lap_handle h, double *h_out, int32_t cap, int32_t *co
     lap_status st = get_history(*h, h_out, cap, &c);
     *count = c;
     return st;
+}
+
+lap_status lap_get_lanczos(lap_handle h, double *h_alpha, double *h_beta, int32_t cap, int32_t *count)
+{
+    if (!h || !count || h->host_only || (cap > 0 && !h_alpha && !h_beta)) return LAP_ERR_INVALID_ARG;
+    int c = 0;
+    lap_status st = get_lanczos(*h, h_alpha, h_beta, cap, &c);
+    *count = c;
+    return st;
+}
+
+lap_status lap_estimate_condition(lap_handle h, int32_t *steps, double *lambda_min, double *lambda_max)
+{
+    if (!h || h->host_only || !lambda_min || !lambda_max) return LAP_ERR_INVALID_ARG;
+    if (h->m.opt.prec == LAP_PREC_PEGP_INNER) return LAP_ERR_UNSUPPORTED;
+    int c = 0;
+    lap_status st = get_lanczos(*h, nullptr, nullptr, 0, &c);
+    if (st != LAP_OK) return st;
+    if (c < 1) return LAP_ERR_INVALID_ARG;
+    std::vector<double> al(static_cast<size_t>(c)), be(static_cast<size_t>(c));
+    st = get_lanczos(*h, al.data(), be.data(), c, &c);
+    if (st != LAP_OK) return st;
+    std::vector<double> a, b;
+    if (!lanczos_tridiagonal(al.data(), be.data(), c, a, b)) return LAP_ERR_BREAKDOWN;
+    if (!tridiag_extremes(a, b, lambda_min, lambda_max)) return LAP_ERR_BREAKDOWN;
+    if (steps) *steps = c;
+    return LAP_OK;
 }
 
 lap_status lap_get_hierarchy_info(lap_handle h, lap_hierarchy_info *info)

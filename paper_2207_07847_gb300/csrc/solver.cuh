@@ -11,6 +11,7 @@
 
 namespace lap {
 struct BatchWork;   // batched-solve workspace (batched.cu)
+struct GmState;     // FGMRES cycle state (fgmres.cuh)
 }
 
 struct lap_handle_s {
@@ -30,6 +31,9 @@ struct lap_handle_s {
     lap::DevMsp<float> M32;
     lap::DevCsr<double> H64;          // L_H (PEGP), expanded tree order
     lap::DevCsr<float> H32;
+    double *G64 = nullptr;            // exact PEGP: dense L_H^+ (up to a constant), tree order
+    float *G32 = nullptr;             // its FP32 copy (mixed precision)
+    int64_t g_ld = 0;                 // leading dimension of G64 / G32
     int tpr = 8, tprH = 8;            // threads per CSR row
 
     int *perm1 = nullptr;             // tree position -> input vertex id
@@ -51,6 +55,16 @@ struct lap_handle_s {
     double *hist = nullptr;           // device history of the last solve (maxit entries)
     int hist_count = 0;
     int hist_capacity = 0;
+    double *lz = nullptr;             // (alpha, beta) per outer step, 2 * hist_capacity
+    int lz_run = 0;                   // steps of the last solve's first CG run
+    // FGMRES (allocated by the first FGMRES solve): basis V (m + 1 columns),
+    // preconditioned vectors Z (m columns), cycle state, dot partials, and
+    // the captured cycle
+    double *gm_V = nullptr, *gm_Z = nullptr, *gm_part = nullptr;
+    lap::GmState *gm = nullptr;
+    int gm_m = 0;
+    cudaGraphExec_t g_gm = nullptr;
+    int64_t nodes_gm = 0;
     std::shared_ptr<lap::BatchWork> batch;   // allocated by the first batched solve
     int batch_ct[6] = {0, 0, 0, 0, 0, 0};   // tuned column tile per batch width 8..256
 };
@@ -73,6 +87,7 @@ lap_status solve_host(lap_handle_s &h, const double *b, double *x, cudaStream_t 
                       lap_solve_info &info);
 lap_status update_options(lap_handle_s &h, const lap_options &o);
 lap_status get_history(lap_handle_s &h, double *out, int cap, int *count);
+lap_status get_lanczos(lap_handle_s &h, double *alpha, double *beta, int cap, int *count);
 lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, double *ms,
                         double *bytes);
 

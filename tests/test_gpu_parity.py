@@ -125,11 +125,13 @@ def test_msp_solve_solves_the_sparsifier(case):
     assert np.linalg.norm(d) <= 1e-9 * np.linalg.norm(want)
 
 
-@pytest.mark.parametrize("kind", ["msp", "none", "pegp_inner"])
+@pytest.mark.parametrize("kind", ["msp", "none", "pegp_inner", "pegp_exact"])
 def test_preconditioner_apply(case, kind):
     name, g, ho, ops = case
     if kind == "pegp_inner" and name not in ("grid2d_64", "grid3d_20"):
         pytest.skip("PEGP inner solve checked on the grid cases")
+    if kind == "pegp_exact" and name == "grid3d_20":
+        pytest.skip("dense inverse checked on the four smaller expanded graphs")
     h = P.lap_setup(g, seed=17, mu=0.8, prec=kind, inner_tol=1e-10, inner_maxit=2000)
     r = gg.rhs(g.n, seed=5)
     z = dev(np.zeros(g.n))
@@ -207,6 +209,187 @@ def test_fp64_pegp_inner_parity():
     xg = host(x)
     assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
     assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+
+
+@pytest.mark.parametrize("mu", [1 / 64, 0.3, 0.8])
+def test_fp64_pegp_exact_parity(mu):
+    """The small workload (2D 64 x 64 grid, weights U[1, 2], coarsened to <= 32
+    vertices) with the exact PEGP: the device applies a dense inverse of the
+    scaled L_H, the oracle a sparse LU solve of L_H; mu = 1/sqrt(n) is the
+    paper's choice for bounded condition numbers (Section 4)."""
+    g = SMALL["grid2d_64"]()
+    b = gg.rhs(g.n, seed=2)
+    h = P.lap_setup(g, seed=17, mu=mu, prec="pegp_exact")
+    x, info = solve_gpu(h, dev(b))
+    ref = _oracle_solve(g, b, "pegp_exact", mu)
+    assert info.status == 0 and ref.converged
+    _check_trajectory(h, info, ref)
+    assert abs(info.iterations - ref.iters) <= 1
+    L = laplacian(g.adjacency())
+    bp = b - b.mean()
+    xg = host(x)
+    assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
+    assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+    assert info.inner_iterations == 0
+
+
+def test_pegp_exact_ragged_and_mixed():
+    """Expanded sizes that are not a multiple of the 64-wide elimination block,
+    FP32 copies of the inverse in mixed precision, and the dense matvec's
+    roofline figures."""
+    g = gg.grid2d(23, 17, weights="loguniform", lo=1e-2, hi=1e2, seed=5)
+    b = gg.rhs(g.n, seed=3)
+    ref = _oracle_solve(g, b, "pegp_exact", 0.5)
+    info_h = None
+    for precision in ("fp64", "mixed"):
+        h = P.lap_setup(g, seed=17, mu=0.5, prec="pegp_exact", precision=precision)
+        info_h = P.lap_get_hierarchy_info(h)
+        assert info_h["ntilde"] % 64 != 0
+        x, info = solve_gpu(h, dev(b))
+        assert info.status == 0 and info.relres <= 1e-8, info.as_dict()
+        if precision == "fp64":
+            assert abs(info.iterations - ref.iters) <= 1
+        L = laplacian(g.adjacency())
+        bp = b - b.mean()
+        assert np.linalg.norm(L @ (host(x) - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+        ms, by = P.lap_kernel_bench(h, "pegp_gemv", 1 if precision == "mixed" else 0, 3)
+        s = 4 if precision == "mixed" else 8
+        assert by == pytest.approx(s * info_h["ntilde"] ** 2 + 2 * s * info_h["ntilde"])
+        assert ms > 0
+
+
+def test_pegp_exact_size_cap():
+    """Expanded graphs above 16384 vertices are not inverted densely."""
+    g = gg.grid2d(100, weights="uniform", lo=1.0, hi=2.0, seed=1)
+    with pytest.raises(P.LapError) as e:
+        P.lap_setup(g, seed=17, mu=0.1, prec="pegp_exact")
+    assert e.value.status == 12
+
+
+@pytest.mark.parametrize("kind,mu", [("none", 0.8), ("msp", 0.8), ("pegp_exact", 1 / 64),
+                                     ("pegp_exact", 0.8)])
+def test_lanczos_coefficients_and_condition_estimate(kind, mu):
+    """CG's alpha_j and beta_j recorded on the device equal the oracle's step by
+    step; the library's bisection on the Lanczos tridiagonal equals a dense
+    eigensolve of the same tridiagonal; the exact PEGP's spectrum stays below 1
+    (Section 3.2)."""
+    g = SMALL["grid2d_64"]()
+    b = gg.rhs(g.n, seed=2)
+    h = P.lap_setup(g, seed=17, mu=mu, prec=kind, maxit=3000, tol=1e-10)
+    x, info = solve_gpu(h, dev(b))
+    ref = _oracle_solve(g, b, kind, mu, maxit=3000, tol=1e-10)
+    assert info.status == 0 and ref.converged
+    a, be = P.lap_get_lanczos(h)
+    assert len(a) == info.iterations if info.restarts == 0 else len(a) <= info.iterations
+    m = min(12, len(a), len(ref.alphas))
+    np.testing.assert_allclose(a[:m], ref.alphas[:m], rtol=1e-9)
+    np.testing.assert_allclose(be[:m - 1], ref.betas[:m - 1], rtol=1e-9)
+    assert be[-1] == 0.0
+    k, lo, hi = P.lap_estimate_condition(h)
+    assert k == len(a)
+    lo_d, hi_d = oracle.lanczos_extremes(a, be[:-1])
+    assert lo == pytest.approx(lo_d, rel=1e-10) and hi == pytest.approx(hi_d, rel=1e-12)
+    lo_o, hi_o = oracle.lanczos_extremes(ref.alphas, ref.betas)
+    assert hi == pytest.approx(hi_o, rel=1e-6) and lo == pytest.approx(lo_o, rel=1e-3)
+    if kind == "pegp_exact":
+        assert hi <= 1.0 + 1e-8
+
+
+def test_pegp_condition_numbers_follow_tables_1_and_2():
+    """Tables 1-2 style sweep on unit-weight 2D grids with the exact PEGP:
+    kappa(L_H^+ L_Gt) grows with n at mu = 0.8 and stays below 2 at
+    mu = 1/sqrt(n) (estimated by the Lanczos Ritz values of converged solves)."""
+    kap = {}
+    for side in (16, 32, 64):
+        g = gg.grid2d(side, weights="uniform", lo=1.0, hi=1.0, seed=1)
+        b = gg.rhs(g.n, seed=3)
+        for mu in (0.8, 1.0 / side):
+            h = P.lap_setup(g, seed=1, mu=mu, prec="pegp_exact", tol=1e-12, maxit=2000)
+            x, info = solve_gpu(h, dev(b))
+            assert info.status == 0
+            k, lo, hi = P.lap_estimate_condition(h)
+            assert hi <= 1.0 + 1e-8
+            kap[(side, mu)] = hi / lo
+    assert kap[(16, 0.8)] < kap[(32, 0.8)] < kap[(64, 0.8)]
+    for side in (16, 32, 64):
+        assert kap[(side, 1.0 / side)] < 2.0 < kap[(side, 0.8)]
+
+
+def test_condition_estimate_refusals():
+    g = gg.grid2d(12, weights="uniform", seed=1)
+    h = P.lap_setup(g, seed=1, prec="msp")
+    with pytest.raises(P.LapError) as e:
+        P.lap_estimate_condition(h)                      # no solve yet
+    assert e.value.status == 1
+    h = P.lap_setup(g, seed=1, prec="pegp_inner")
+    solve_gpu(h, dev(gg.rhs(g.n, seed=1)))
+    with pytest.raises(P.LapError) as e:
+        P.lap_estimate_condition(h)                      # flexible CG
+    assert e.value.status == 12
+    h = P.lap_setup(g, seed=1, prec="msp", precision="mixed")
+    solve_gpu(h, dev(gg.rhs(g.n, seed=1)))
+    k, lo, hi = P.lap_estimate_condition(h)              # the first FP32 inner solve
+    assert k >= 1 and 0.0 < lo <= hi
+
+
+FGMRES_CASES = {
+    # name: (graph, preconditioner, mu, restart, extra options)
+    "grid2d_64_msp": (lambda: SMALL["grid2d_64"](), "msp", 0.8, 30, {}),
+    "grid2d_64_pegp_exact": (lambda: SMALL["grid2d_64"](), "pegp_exact", 1 / 64, 30, {}),
+    "grid2d_64_pegp_inner": (lambda: SMALL["grid2d_64"](), "pegp_inner", 0.8, 30,
+                             {"inner_tol": 1e-6, "inner_maxit": 500}),
+    "grid2d_24_none": (lambda: gg.grid2d(24, weights="uniform", lo=1.0, hi=2.0, seed=1), "none",
+                       0.8, 30, {}),
+    "chunglu_4k_msp_r5": (lambda: SMALL["chunglu_4k"](), "msp", 0.8, 5, {}),
+    "rmat_11_msp_r8": (lambda: SMALL["rmat_11"](), "msp", 0.8, 8, {}),
+}
+
+
+@pytest.mark.parametrize("name", list(FGMRES_CASES))
+def test_fgmres_parity(name):
+    """Flexible GMRES(m), the paper's outer method (Section 4), against the
+    oracle's: residual histories step by step (classical Gram-Schmidt twice on
+    the device, modified Gram-Schmidt in the oracle: equal in exact
+    arithmetic), iteration and cycle counts, the solution."""
+    make, kind, mu, restart, kw = FGMRES_CASES[name]
+    g = make()
+    b = gg.rhs(g.n, seed=7)
+    h = P.lap_setup(g, seed=17, mu=mu, prec=kind, krylov="fgmres", restart=restart, maxit=3000,
+                    **kw)
+    x, info = solve_gpu(h, dev(b))
+    ref = oracle.solve(g, b, kind, mu=mu, seed=17, krylov="fgmres", restart=restart, maxit=3000,
+                       **kw)
+    assert info.status == 0 and ref.converged, info.as_dict()
+    hist = P.lap_get_history(h)
+    assert len(hist) == info.iterations
+    inexact = kind == "pegp_inner"          # inner solves stop at 1e-6 on both sides
+    m = min(5 if inexact else 12, len(hist), len(ref.history))
+    np.testing.assert_allclose(hist[:m], ref.history[:m], rtol=1e-5 if inexact else 1e-9,
+                               atol=1e-13)
+    assert abs(info.iterations - ref.iters) <= max(1, int(round(0.03 * ref.iters)))
+    assert abs(info.restarts - ref.restarts) <= 1
+    L = laplacian(g.adjacency())
+    bp = b - b.mean()
+    xg = host(x)
+    assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
+    assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+    assert abs(xg.mean()) <= 1e-12 * np.abs(xg).max()
+
+
+def test_fgmres_limits():
+    g = gg.grid2d(24, weights="uniform", lo=1.0, hi=2.0, seed=1)
+    b = dev(gg.rhs(g.n, seed=1))
+    h = P.lap_setup(g, seed=17, prec="msp", krylov="fgmres", restart=10, maxit=7)
+    x, info = solve_gpu(h, b)
+    assert info.status == 7 and info.iterations == 7 and info.relres > 1e-8
+    P.lap_update_options(h, maxit=1000, restart=3)          # a new cycle length
+    x, info = solve_gpu(h, b)
+    assert info.status == 0 and info.restarts >= 1
+    h = P.lap_setup(g, seed=17, prec="msp", precision="mixed", krylov="fgmres")
+    x, info = solve_gpu(h, b)
+    assert info.status == 12                                 # FP64 only
+    with pytest.raises(P.LapError):
+        P.lap_setup(g, seed=17, prec="msp", krylov="fgmres", restart=129)
 
 
 @pytest.mark.parametrize("kind", ["msp", "pegp_inner"])

@@ -411,8 +411,12 @@ def bench_powerlaw(args, dev, world):
     x = torch.empty(g.n, dtype=torch.float64, device=dev)
     out = {"workload": f"chunglu_{args.powerlaw_n}_d16_g2.5_uniform01_MSP_mu0.8", "n": g.n,
            "nnz": P.lap_get_hierarchy_info(h)["nnz"], "gen_s": round(gen_s, 2), "setup_s": round(setup_s, 2)}
-    for precision in ("mixed", "fp64"):
-        P.lap_update_options(h, precision=precision)
+    for precision in ("mixed", "fp64", "fgmres"):
+        # "fgmres": the paper's outer method, flexible GMRES(30), FP64
+        if precision == "fgmres":
+            P.lap_update_options(h, precision="fp64", krylov="fgmres", restart=30)
+        else:
+            P.lap_update_options(h, precision=precision)
         bs = [torch.as_tensor(gg.rhs(g.n, seed=800 + i), device=dev) for i in range(4)]
         P.lap_pcg_solve(h, bs[0], x)                                 # warm-up
         ranks_barrier(world)
@@ -466,6 +470,16 @@ def bench_pegp_exact(args, dev, world):
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     k_l, lo_l, hi_l = P.lap_estimate_condition(h)
     nt = info_h["ntilde"]
+    # the paper's outer method on the same system: flexible GMRES(30)
+    P.lap_update_options(h, krylov="fgmres", restart=30)
+    P.lap_pcg_solve(h, bs[0], x)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ginfos = [P.lap_pcg_solve(h, b, x) for b in bs[3:13]]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    P.lap_update_options(h, krylov="cg")
     m64, b64 = P.lap_kernel_bench(h, "pegp_gemv", 0, 20)
     m32, b32 = P.lap_kernel_bench(h, "pegp_gemv", 1, 20)
     out = {"workload": f"grid2d_{side}x{side}_uniform[1,2]_PEGP_exact_mu1/sqrt(n)_fp64", "n": g.n,
@@ -476,6 +490,10 @@ def bench_pegp_exact(args, dev, world):
            "relres_max": max(i.relres for i in infos),
            "failed": sum(1 for i in infos if i.status != 0),
            "lanczos": {"steps": k_l, "lambda_min": lo_l, "lambda_max": hi_l, "kappa": hi_l / lo_l},
+           "fgmres": {"value": whole_job_rate(len(ginfos), world, gms), "unit": "solves/s",
+                      "iterations": [i.iterations for i in ginfos][:5],
+                      "relres_max": max(i.relres for i in ginfos),
+                      "failed": sum(1 for i in ginfos if i.status != 0)},
            "dense_matvec": {
                "fp64": {"us": round(m64 * 1e3, 2), "GB/s": round(b64 / (m64 * 1e-3) / 1e9, 1),
                         "bound": "alu", "TFLOP/s": round(2.0 * nt * nt / (m64 * 1e-3) / 1e12, 3),

@@ -65,6 +65,7 @@ template <typename V> struct DevCsr {
     int64_t ell_entries = 0, long_entries = 0;
     int kernel = 0;
     int vec = 1;                       // SELL lane-group width (1, 2, 4)
+    int sell_grid = 0;                 // SELL blocks per launch (0: one per 8 slices, capped)
 };
 
 template <typename V> struct DevMspLevel {

@@ -431,17 +431,33 @@ template <typename V, int MODE>
 void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, const double *bs,
           double *yres, const CgState &st, cudaStream_t s);
 
-int autotune_spmv(lap_handle_s &h, const DevCsr<double> &A, double *x, double *y)
+// Matvec kernel of one matrix copy, chosen by timing: SELL with one, two or
+// three waves of resident blocks (more blocks than fit let the hardware
+// balance slices of uneven cost), or CSR with 2..16 threads per row.  The
+// reductions of SELL launches hold one partial pair per block, so a grid
+// stays within the partials buffer.
+template <typename V>
+void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
 {
-    const int cand[] = {0, 2, 4, 8, 16};
+    struct Cand { int kernel, grid; };
+    std::vector<Cand> cand;
+    const int64_t need = (static_cast<int64_t>(A.nslices + A.nlong) * 32 + kBlock - 1) / kBlock;
+    for (int waves = 1; waves <= 3; ++waves) {
+        const int64_t g = std::min<int64_t>(need, int64_t(h.grid_cap) * waves);
+        if (g > kMaxRedBlocks * kRedSlots / 2) break;
+        if (waves > 1 && g <= int64_t(h.grid_cap) * (waves - 1)) break;   // no new launch shape
+        cand.push_back({-1, static_cast<int>(std::max<int64_t>(g, 1))});
+    }
+    for (int t : {2, 4, 8, 16}) cand.push_back({t, 0});
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 0;
-    int best = 0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return;
+    Cand best = cand[0];
     float best_ms = 1e30f;
-    for (int c : cand) {
-        spmv<double, 2>(h, A, c < 1 ? -1 : c, x, y, nullptr, nullptr, h.stb, h.s);
+    for (const Cand &c : cand) {
+        A.sell_grid = c.grid;
+        spmv<V, 2>(h, A, c.kernel, x, y, nullptr, nullptr, h.stb, h.s);
         cudaEventRecord(e0, h.s);
-        for (int i = 0; i < 5; ++i) spmv<double, 2>(h, A, c < 1 ? -1 : c, x, y, nullptr, nullptr, h.stb, h.s);
+        for (int i = 0; i < 5; ++i) spmv<V, 2>(h, A, c.kernel, x, y, nullptr, nullptr, h.stb, h.s);
         cudaEventRecord(e1, h.s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -454,7 +470,8 @@ int autotune_spmv(lap_handle_s &h, const DevCsr<double> &A, double *x, double *y
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     (void)cudaGetLastError();
-    return best;
+    A.kernel = best.kernel < 0 ? 0 : best.kernel;
+    A.sell_grid = best.grid;
 }
 
 // --------------------------------------------------------------------------
@@ -473,7 +490,8 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
                 MODE != 2);
         }
         h.launches += 1;
-        const int g = grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
+        const int g = A.sell_grid > 0 ? A.sell_grid
+                                      : grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
 #define LAP_SELL(VEC)                                                                                   \
     k_sell<V, MODE, VEC><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.rowperm, A.eci, A.ew, A.nlong, A.lrow, \
                                               A.lchunk_ptr, A.chunk_part, x, y, bs, yres, st.sc, st.part,   \
@@ -1440,8 +1458,13 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
     if (m.opt.spmv_tpr != 0) {
         h.L64.kernel = h.L32.kernel = h.H64.kernel = h.H32.kernel = std::max(m.opt.spmv_tpr, 0);
     } else {
-        h.L64.kernel = h.L32.kernel = autotune_spmv(h, h.L64, h.w64.p, h.w64.q);
-        if (m.has_LH) h.H64.kernel = h.H32.kernel = autotune_spmv(h, h.H64, h.e64.p, h.e64.q);
+        // each copy on its own: the FP64 and FP32 matvecs prefer different shapes
+        autotune_spmv<double>(h, h.L64, h.w64.p, h.w64.q);
+        if (mixed) autotune_spmv<float>(h, h.L32, h.w32.p, h.w32.q);
+        if (m.has_LH) {
+            autotune_spmv<double>(h, h.H64, h.e64.p, h.e64.q);
+            if (mixed) autotune_spmv<float>(h, h.H32, h.e32.p, h.e32.q);
+        }
     }
     LAP_CK(cudaDeviceSynchronize());
     return LAP_OK;

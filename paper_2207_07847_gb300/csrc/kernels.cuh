@@ -329,6 +329,8 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
 // SELL-32 matvec in edge-difference form: one warp per slice of 32 rows,
 // lane l owning the row of slot 32 s + l and reading its entries VEC at a
 // time (see make_sell for the layout); long rows add their chunk partials.
+// The warps stride over the slices; the grid (one or more waves of resident
+// blocks) is chosen per matrix at setup by timing.
 template <typename V, int MODE, int VEC>
 __global__ void __launch_bounds__(kBlock)
 k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__restrict__ lmask,
@@ -343,30 +345,32 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     double a0 = 0.0, a1 = 0.0;
+    auto slice = [&](int task) {
+        const int slot = task * 32 + lane;
+        const int row = rowperm ? rowperm[slot] : (slot < n ? slot : -1);
+        const bool valid = row >= 0;
+        const int64_t base = sptr[task];
+        const int width = static_cast<int>((sptr[task + 1] - base) >> 5);
+        const V xi = valid ? x[row] : V(0);
+        V s = V(0);
+        const int *pc = eci + base + lane * VEC;
+        const V *pw = ew + base + lane * VEC;
+        const int ng = width / VEC;
+#pragma unroll(VEC == 1 ? 4 : 2)
+        for (int g = 0; g < ng; ++g) s = LaneGroup<V, VEC>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
+        if (valid && !((lmask[task] >> lane) & 1u)) spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
+    };
+    auto long_row = [&](int li) {
+        // long row: add its chunk partials in chunk order
+        const int row = lrow[li];
+        V s = V(0);
+        for (int c = lchunk_ptr[li]; c < lchunk_ptr[li + 1]; ++c) s += chunk_part[c];
+        spmv_finish<V, MODE>(row, x[row], s, y, bs, yres, a0, a1);
+    };
     const int ntask = nslices + nlong;
     for (int task = gwarp; task < ntask; task += nwarp) {          // warp-uniform
-        if (task < nslices) {
-            const int slot = task * 32 + lane;
-            const int row = rowperm ? rowperm[slot] : (slot < n ? slot : -1);
-            const bool valid = row >= 0;
-            const int64_t base = sptr[task];
-            const int width = static_cast<int>((sptr[task + 1] - base) >> 5);
-            const V xi = valid ? x[row] : V(0);
-            V s = V(0);
-            const int *pc = eci + base + lane * VEC;
-            const V *pw = ew + base + lane * VEC;
-            const int ng = width / VEC;
-#pragma unroll(VEC == 1 ? 4 : 2)
-            for (int g = 0; g < ng; ++g) s = LaneGroup<V, VEC>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
-            if (valid && !((lmask[task] >> lane) & 1u)) spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
-        } else if (lane == 0) {
-            // long row: add its chunk partials in chunk order
-            const int li = task - nslices;
-            const int row = lrow[li];
-            V s = V(0);
-            for (int c = lchunk_ptr[li]; c < lchunk_ptr[li + 1]; ++c) s += chunk_part[c];
-            spmv_finish<V, MODE>(row, x[row], s, y, bs, yres, a0, a1);
-        }
+        if (task < nslices) slice(task);
+        else if (lane == 0) long_row(task - nslices);
     }
     if (MODE == 2) return;
     double v[2] = {a0, a1};

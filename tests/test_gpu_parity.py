@@ -281,7 +281,11 @@ def test_lanczos_coefficients_and_condition_estimate(kind, mu):
     assert info.status == 0 and ref.converged
     a, be = P.lap_get_lanczos(h)
     assert len(a) == info.iterations if info.restarts == 0 else len(a) <= info.iterations
-    m = min(12, len(a), len(ref.alphas))
+    # step by step while the residual is well above rounding: alpha_j and
+    # beta_j carry the two summation orders' rounding divided by the residual
+    # (R6), so steps after the residual falls below 1e-5 are left out
+    hist = np.asarray(ref.history)
+    m = min(12, len(a), len(ref.alphas), 1 + int(np.sum(hist > 1e-5)))
     np.testing.assert_allclose(a[:m], ref.alphas[:m], rtol=1e-9)
     np.testing.assert_allclose(be[:m - 1], ref.betas[:m - 1], rtol=1e-9)
     assert be[-1] == 0.0

@@ -41,7 +41,7 @@ FP64_ALU_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (no measured figu
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current
 # kernel, scaled to the 128^3 workload (profiles/k_sell_f32_LH_grid3d96.md);
 # removed whenever the kernel changes.
-MEASURED_TRAFFIC = {"spmv_LH": 1.841e9}
+MEASURED_TRAFFIC = {"spmv_LH": 1.843e9}
 
 
 def parse():

@@ -3,14 +3,61 @@
 // multilevel sparsifier T (Section 3.3), the top-level pseudo-inverse and, for
 // PEGP, the Laplacian of the positively weighted expanded graph H (Section 3.2).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <new>
 #include <numeric>
+#include <thread>
 #include <utility>
 
 #include "lap_internal.h"
 
 namespace lap {
+namespace {
+
+// Host worker threads for the setup loops whose results do not depend on how
+// the work is split (each output is computed by one thread, in the same
+// order as the sequential loop would): at most 16 (or LAP_SETUP_THREADS from
+// the environment), one for small inputs.
+int setup_threads(int64_t work)
+{
+    if (work < (int64_t(1) << 16)) return 1;
+    unsigned cap = 16;
+    if (const char *e = std::getenv("LAP_SETUP_THREADS")) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v >= 1 && v <= 256) cap = static_cast<unsigned>(v);
+    }
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    return static_cast<int>(std::min(hw, cap));
+}
+
+// fn(t, begin, end) on T contiguous chunks of [0, n); a failed allocation in
+// any worker is rethrown on the calling thread.
+template <typename Fn>
+void parallel_chunks(int64_t n, int T, Fn fn)
+{
+    if (T <= 1) {
+        fn(0, int64_t(0), n);
+        return;
+    }
+    std::atomic<bool> oom{false};
+    std::vector<std::thread> th;
+    th.reserve(static_cast<size_t>(T));
+    for (int t = 0; t < T; ++t)
+        th.emplace_back([&, t] {
+            try {
+                fn(t, n * t / T, n * (t + 1) / T);
+            } catch (const std::bad_alloc &) {
+                oom = true;
+            }
+        });
+    for (auto &x : th) x.join();
+    if (oom) throw std::bad_alloc();
+}
+
+}  // namespace
 
 uint64_t splitmix64(uint64_t seed, uint64_t i)
 {
@@ -168,33 +215,49 @@ void coarse_graph(const HostLevel &F, int64_t nc, HostLevel &C)
         for (int64_t u = 0; u < n; ++u) members[cursor[F.agg[u]]++] = static_cast<int32_t>(u);
     }
     C.n = nc;
+    // coarse rows by ranges of aggregates; within an aggregate its members
+    // are visited in increasing id and their CSR entries in order, so every
+    // coarse weight is summed in the same order as one sequential pass
+    const int T = setup_threads(F.rp[n]);
+    std::vector<std::vector<int32_t>> pci(static_cast<size_t>(T));
+    std::vector<std::vector<double>> pw(static_cast<size_t>(T));
+    std::vector<int64_t> rowlen(static_cast<size_t>(nc), 0);
+    parallel_chunks(nc, T, [&](int t, int64_t I0, int64_t I1) {
+        std::vector<double> acc(static_cast<size_t>(nc), 0.0);
+        std::vector<int32_t> stamp(static_cast<size_t>(nc), -1);
+        std::vector<int32_t> cols;
+        for (int64_t I = I0; I < I1; ++I) {
+            cols.clear();
+            for (int64_t q = start[I]; q < start[I + 1]; ++q) {
+                const int32_t u = members[q];
+                for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) {
+                    const int32_t J = F.agg[F.ci[p]];
+                    if (J == I) continue;
+                    if (stamp[J] != I) {
+                        stamp[J] = static_cast<int32_t>(I);
+                        acc[J] = 0.0;
+                        cols.push_back(J);
+                    }
+                    acc[J] += F.w[p];
+                }
+            }
+            std::sort(cols.begin(), cols.end());
+            for (int32_t J : cols) {
+                pci[t].push_back(J);
+                pw[t].push_back(acc[J]);
+            }
+            rowlen[I] = static_cast<int64_t>(cols.size());
+        }
+    });
     C.rp.assign(static_cast<size_t>(nc) + 1, 0);
+    for (int64_t I = 0; I < nc; ++I) C.rp[I + 1] = C.rp[I] + rowlen[I];
     C.ci.clear();
     C.w.clear();
-    std::vector<double> acc(static_cast<size_t>(nc), 0.0);
-    std::vector<int32_t> stamp(static_cast<size_t>(nc), -1);
-    std::vector<int32_t> cols;
-    for (int64_t I = 0; I < nc; ++I) {
-        cols.clear();
-        for (int64_t t = start[I]; t < start[I + 1]; ++t) {
-            const int32_t u = members[t];
-            for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) {
-                const int32_t J = F.agg[F.ci[p]];
-                if (J == I) continue;
-                if (stamp[J] != I) {
-                    stamp[J] = static_cast<int32_t>(I);
-                    acc[J] = 0.0;
-                    cols.push_back(J);
-                }
-                acc[J] += F.w[p];
-            }
-        }
-        std::sort(cols.begin(), cols.end());
-        for (int32_t J : cols) {
-            C.ci.push_back(J);
-            C.w.push_back(acc[J]);
-        }
-        C.rp[I + 1] = static_cast<int64_t>(C.ci.size());
+    C.ci.reserve(static_cast<size_t>(C.rp[nc]));
+    C.w.reserve(static_cast<size_t>(C.rp[nc]));
+    for (int t = 0; t < T; ++t) {
+        C.ci.insert(C.ci.end(), pci[t].begin(), pci[t].end());
+        C.w.insert(C.w.end(), pw[t].begin(), pw[t].end());
     }
 }
 
@@ -281,86 +344,132 @@ void build_pegp(HostModel &m)
     // expanded index in tree order
     auto xidx = [&](int k, int64_t u) { return m.offset[k] + m.lev[k].pos[u]; };
 
-    EdgeAcc E;
-    std::vector<int32_t> anc_u;     // ancestor chain scratch
-    std::vector<int32_t> nbr_anc;   // current ancestor of each neighbour
-    std::vector<double> nbr_w;
-    std::vector<std::pair<int32_t, double>> grp;
+    // every kept edge is produced once, by the finer endpoint u (same-level
+    // edges by their smaller end), with a weight computed from u's row alone;
+    // the threads split the vertices of each level, so the edge set and every
+    // weight are those of one sequential pass
+    std::vector<EdgeAcc> parts;
     for (int k = 0; k < l; ++k) {
         const HostLevel &L = m.lev[k];
-        for (int64_t u = 0; u < L.n; ++u) {
-            const int64_t deg = L.rp[u + 1] - L.rp[u];
-            nbr_anc.resize(static_cast<size_t>(deg));
-            nbr_w.resize(static_cast<size_t>(deg));
-            for (int64_t t = 0; t < deg; ++t) {
-                nbr_anc[t] = L.ci[L.rp[u] + t];
-                nbr_w[t] = L.w[L.rp[u] + t];
-                // same-level edge (k, k): weight mu^(2k) w; store once (u < v)
-                if (nbr_anc[t] > u)
-                    E.i.push_back(xidx(k, u)), E.j.push_back(xidx(k, nbr_anc[t])),
-                        E.w.push_back(mpow[2 * k] * nbr_w[t]);
-            }
-            int32_t a = static_cast<int32_t>(u);
-            for (int j = k + 1; j < l; ++j) {
-                const std::vector<int32_t> &up = m.lev[j - 1].agg;
-                a = up[a];
-                for (int64_t t = 0; t < deg; ++t) nbr_anc[t] = up[nbr_anc[t]];
-                const double scale = mpow[k + j];
-                if ((j - k) % 2 == 1) {
-                    double out = 0.0;
-                    for (int64_t t = 0; t < deg; ++t)
-                        if (nbr_anc[t] != a) out += nbr_w[t];
-                    if (out > 0.0)
-                        E.i.push_back(xidx(k, u)), E.j.push_back(xidx(j, a)),
-                            E.w.push_back(scale * out);
-                } else {
-                    grp.clear();
-                    for (int64_t t = 0; t < deg; ++t)
-                        if (nbr_anc[t] != a) grp.push_back({nbr_anc[t], nbr_w[t]});
-                    std::stable_sort(grp.begin(), grp.end(),
-                                     [](const auto &x, const auto &y) { return x.first < y.first; });
-                    for (size_t s = 0; s < grp.size();) {
-                        size_t e = s;
-                        double W = 0.0;
-                        while (e < grp.size() && grp[e].first == grp[s].first) W += grp[e++].second;
-                        E.i.push_back(xidx(k, u)), E.j.push_back(xidx(j, grp[s].first)),
-                            E.w.push_back(scale * W);
-                        s = e;
+        const int T = setup_threads(L.rp[L.n] * (l - k));
+        const size_t base = parts.size();
+        parts.resize(base + static_cast<size_t>(T));
+        parallel_chunks(L.n, T, [&](int t, int64_t u0, int64_t u1) {
+            EdgeAcc &E = parts[base + static_cast<size_t>(t)];
+            std::vector<int32_t> nbr_anc;   // current ancestor of each neighbour
+            std::vector<double> nbr_w;
+            std::vector<std::pair<int32_t, double>> grp;
+            for (int64_t u = u0; u < u1; ++u) {
+                const int64_t deg = L.rp[u + 1] - L.rp[u];
+                nbr_anc.resize(static_cast<size_t>(deg));
+                nbr_w.resize(static_cast<size_t>(deg));
+                for (int64_t q = 0; q < deg; ++q) {
+                    nbr_anc[q] = L.ci[L.rp[u] + q];
+                    nbr_w[q] = L.w[L.rp[u] + q];
+                    // same-level edge (k, k): weight mu^(2k) w; stored once (u < v)
+                    if (nbr_anc[q] > u)
+                        E.i.push_back(xidx(k, u)), E.j.push_back(xidx(k, nbr_anc[q])),
+                            E.w.push_back(mpow[2 * k] * nbr_w[q]);
+                }
+                int32_t a = static_cast<int32_t>(u);
+                for (int j = k + 1; j < l; ++j) {
+                    const std::vector<int32_t> &up = m.lev[j - 1].agg;
+                    a = up[a];
+                    for (int64_t q = 0; q < deg; ++q) nbr_anc[q] = up[nbr_anc[q]];
+                    const double scale = mpow[k + j];
+                    if ((j - k) % 2 == 1) {
+                        double out = 0.0;
+                        for (int64_t q = 0; q < deg; ++q)
+                            if (nbr_anc[q] != a) out += nbr_w[q];
+                        if (out > 0.0)
+                            E.i.push_back(xidx(k, u)), E.j.push_back(xidx(j, a)),
+                                E.w.push_back(scale * out);
+                    } else {
+                        grp.clear();
+                        for (int64_t q = 0; q < deg; ++q)
+                            if (nbr_anc[q] != a) grp.push_back({nbr_anc[q], nbr_w[q]});
+                        std::stable_sort(grp.begin(), grp.end(),
+                                         [](const auto &x, const auto &y) { return x.first < y.first; });
+                        for (size_t s = 0; s < grp.size();) {
+                            size_t e = s;
+                            double W = 0.0;
+                            while (e < grp.size() && grp[e].first == grp[s].first) W += grp[e++].second;
+                            E.i.push_back(xidx(k, u)), E.j.push_back(xidx(j, grp[s].first)),
+                                E.w.push_back(scale * W);
+                            s = e;
+                        }
                     }
                 }
             }
-        }
+        });
     }
-    // symmetric CSR over the expanded vertices (tree order), sorted columns
+    // symmetric CSR over the expanded vertices (tree order); every row's
+    // columns are distinct, so sorting them fixes the row whatever order the
+    // edges arrived in
     const int64_t nt = m.offset[l];
     HostCsr &H = m.LH;
     H.n = nt;
-    H.rp.assign(static_cast<size_t>(nt) + 1, 0);
-    for (size_t e = 0; e < E.i.size(); ++e) ++H.rp[E.i[e] + 1], ++H.rp[E.j[e] + 1];
-    std::partial_sum(H.rp.begin(), H.rp.end(), H.rp.begin());
-    H.ci.assign(static_cast<size_t>(H.rp[nt]), 0);
-    H.w.assign(static_cast<size_t>(H.rp[nt]), 0.0);
-    std::vector<int64_t> cur(H.rp.begin(), H.rp.end() - 1);
-    for (size_t e = 0; e < E.i.size(); ++e) {
-        H.ci[cur[E.i[e]]] = static_cast<int32_t>(E.j[e]);
-        H.w[cur[E.i[e]]++] = E.w[e];
-        H.ci[cur[E.j[e]]] = static_cast<int32_t>(E.i[e]);
-        H.w[cur[E.j[e]]++] = E.w[e];
+    {
+        // rows filled by the threads of the edge pass, each over its own
+        // edges, with atomic row counters and cursors (slot order within a
+        // row is then arbitrary; the sort below fixes it)
+        const int T = setup_threads(nt);
+        std::vector<std::atomic<int64_t>> cnt(static_cast<size_t>(nt));
+        for (auto &c : cnt) c.store(0, std::memory_order_relaxed);
+        // thread t takes the t-th slice of every part's edges (balanced
+        // whatever the parts' sizes)
+        auto slice = [&](const EdgeAcc &E, int t) {
+            const size_t m = E.i.size();
+            return std::make_pair(m * t / T, m * (t + 1) / T);
+        };
+        parallel_chunks(T, T, [&](int t, int64_t, int64_t) {
+            for (const EdgeAcc &E : parts) {
+                const auto r = slice(E, t);
+                for (size_t e = r.first; e < r.second; ++e) {
+                    cnt[E.i[e]].fetch_add(1, std::memory_order_relaxed);
+                    cnt[E.j[e]].fetch_add(1, std::memory_order_relaxed);
+                }
+            }
+        });
+        H.rp.assign(static_cast<size_t>(nt) + 1, 0);
+        for (int64_t r = 0; r < nt; ++r) {
+            H.rp[r + 1] = H.rp[r] + cnt[r].load(std::memory_order_relaxed);
+            cnt[r].store(H.rp[r], std::memory_order_relaxed);
+        }
+        H.ci.assign(static_cast<size_t>(H.rp[nt]), 0);
+        H.w.assign(static_cast<size_t>(H.rp[nt]), 0.0);
+        parallel_chunks(T, T, [&](int t, int64_t, int64_t) {
+            for (const EdgeAcc &E : parts) {
+                const auto r = slice(E, t);
+                for (size_t e = r.first; e < r.second; ++e) {
+                    const int64_t a = cnt[E.i[e]].fetch_add(1, std::memory_order_relaxed);
+                    H.ci[a] = static_cast<int32_t>(E.j[e]);
+                    H.w[a] = E.w[e];
+                    const int64_t b = cnt[E.j[e]].fetch_add(1, std::memory_order_relaxed);
+                    H.ci[b] = static_cast<int32_t>(E.i[e]);
+                    H.w[b] = E.w[e];
+                }
+            }
+        });
+        parts.clear();
+        parts.shrink_to_fit();
     }
     H.diag.assign(static_cast<size_t>(nt), 0.0);
-    std::vector<std::pair<int32_t, double>> row;
-    for (int64_t r = 0; r < nt; ++r) {
-        row.clear();
-        for (int64_t p = H.rp[r]; p < H.rp[r + 1]; ++p) row.push_back({H.ci[p], H.w[p]});
-        std::sort(row.begin(), row.end());
-        double d = 0.0;
-        for (size_t t = 0; t < row.size(); ++t) {
-            H.ci[H.rp[r] + t] = row[t].first;
-            H.w[H.rp[r] + t] = row[t].second;
-            d += row[t].second;
+    parallel_chunks(nt, setup_threads(H.rp[nt]), [&](int, int64_t r0, int64_t r1) {
+        std::vector<std::pair<int32_t, double>> row;
+        for (int64_t r = r0; r < r1; ++r) {
+            row.clear();
+            for (int64_t p = H.rp[r]; p < H.rp[r + 1]; ++p) row.push_back({H.ci[p], H.w[p]});
+            std::sort(row.begin(), row.end());
+            double d = 0.0;
+            for (size_t q = 0; q < row.size(); ++q) {
+                H.ci[H.rp[r] + q] = row[q].first;
+                H.w[H.rp[r] + q] = row[q].second;
+                d += row[q].second;
+            }
+            H.diag[r] = d;
         }
-        H.diag[r] = d;
-    }
+    });
     m.has_LH = true;
 }
 
@@ -620,11 +729,14 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
         return t;
     };
     const int64_t unsorted = slices_size();
-    for (int64_t w0 = 0; w0 < n; w0 += kWin) {
-        const int64_t w1 = std::min(n, w0 + kWin);
-        std::stable_sort(S.rowperm.begin() + w0, S.rowperm.begin() + w1,
-                         [&](int32_t a, int32_t b) { return len(a) > len(b); });
-    }
+    const int64_t nwin = (n + kWin - 1) / kWin;
+    parallel_chunks(nwin, setup_threads(n), [&](int, int64_t v0, int64_t v1) {
+        for (int64_t v = v0; v < v1; ++v) {
+            const int64_t w0 = v * kWin, w1 = std::min(n, w0 + kWin);
+            std::stable_sort(S.rowperm.begin() + w0, S.rowperm.begin() + w1,
+                             [&](int32_t a, int32_t b) { return len(a) > len(b); });
+        }
+    });
     // sorting pays only if it saves padding: else keep the rows in place (an
     // empty rowperm: slot = row)
     const bool sorted = slices_size() * 20 < unsorted * 19;
@@ -702,24 +814,26 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
     }
     S.eci.assign(static_cast<size_t>(S.sptr[S.nslices]), 0);
     S.ew.assign(static_cast<size_t>(S.sptr[S.nslices]), 0.0);
-    for (int64_t s = 0; s < S.nslices; ++s) {
-        const int64_t w = (S.sptr[s + 1] - S.sptr[s]) / 32;
-        for (int64_t lane = 0; lane < 32; ++lane) {
-            const int64_t slot = 32 * s + lane;
-            const int64_t r = slot < n ? S.rowperm[slot] : -1;
-            const bool real = r >= 0 && !((S.longmask[s] >> lane) & 1u);
-            const int64_t d = real ? A.rp[r + 1] - A.rp[r] : 0;
-            for (int64_t j = 0; j < w; ++j) {
-                const int64_t q = S.sptr[s] + (j / vec) * 32 * vec + lane * vec + j % vec;
-                if (j < d) {
-                    S.eci[q] = A.ci[A.rp[r] + j];
-                    S.ew[q] = A.w[A.rp[r] + j];
-                } else {
-                    S.eci[q] = static_cast<int32_t>(r >= 0 ? r : 0);   // weight 0: no contribution
+    parallel_chunks(S.nslices, setup_threads(S.sptr[S.nslices]), [&](int, int64_t s0, int64_t s1) {
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t w = (S.sptr[s + 1] - S.sptr[s]) / 32;
+            for (int64_t lane = 0; lane < 32; ++lane) {
+                const int64_t slot = 32 * s + lane;
+                const int64_t r = slot < n ? S.rowperm[slot] : -1;
+                const bool real = r >= 0 && !((S.longmask[s] >> lane) & 1u);
+                const int64_t d = real ? A.rp[r + 1] - A.rp[r] : 0;
+                for (int64_t j = 0; j < w; ++j) {
+                    const int64_t q = S.sptr[s] + (j / vec) * 32 * vec + lane * vec + j % vec;
+                    if (j < d) {
+                        S.eci[q] = A.ci[A.rp[r] + j];
+                        S.ew[q] = A.w[A.rp[r] + j];
+                    } else {
+                        S.eci[q] = static_cast<int32_t>(r >= 0 ? r : 0);   // weight 0: no contribution
+                    }
                 }
             }
         }
-    }
+    });
     if (!sorted) S.rowperm.clear();
 }
 

@@ -93,6 +93,32 @@ def test_sparsifier_and_pegp_edges_bit_exact(name, make, mu):
     assert P.lap_get_hierarchy_info(h)["edges_T"] == len(ops.T_edges[0])
 
 
+def test_threaded_setup_equals_single_threaded_and_oracle(monkeypatch):
+    """Setup splits its large loops (coarse graphs, H's edges and rows, the
+    SELL layout) over host threads; every output is produced by one thread in
+    the sequential order, so one thread and many give the same bits, and the
+    oracle's integer outputs."""
+    g = gg.grid3d(24, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    outs = []
+    for threads in ("1", "8"):
+        monkeypatch.setenv("LAP_SETUP_THREADS", threads)
+        h = P.lap_setup(g, host_only=1, seed=11, mu=0.8, prec="pegp_inner")
+        info = P.lap_get_hierarchy_info(h)
+        got = [P.lap_get_expanded_edges(h, which) for which in (0, 1)]
+        got += [P.lap_get_aggregates(h, k + 1) for k in range(info["levels"] - 1)]
+        outs.append(got)
+    for a, b in zip(outs[0], outs[1]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=11)
+    ops = oracle.expanded_operators(ho, 0.8, with_LG=False)
+    i, j, w = outs[1][0]
+    np.testing.assert_array_equal(i, ops.H_edges[0])
+    np.testing.assert_array_equal(j, ops.H_edges[1])
+    for k in range(ho.levels - 1):
+        np.testing.assert_array_equal(outs[1][2 + k][0], ho.agg[k])
+
+
 def test_library_reproduces_table_level_sizes():
     for n in (16, 64, 256, 1024):
         s = int(round(n ** 0.5))

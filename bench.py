@@ -480,6 +480,10 @@ def bench_pegp_exact(args, dev, world):
     torch.cuda.synchronize()
     gms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     P.lap_update_options(h, krylov="cg")
+    # stretch of H over T (Section 3.3), tr(L_T^+ L_H) by 32 Hutchinson samples
+    t0 = time.perf_counter()
+    sv = P.lap_estimate_stretch(h, samples=32, seed=1)
+    stretch_s = time.perf_counter() - t0
     m64, b64 = P.lap_kernel_bench(h, "pegp_gemv", 0, 20)
     m32, b32 = P.lap_kernel_bench(h, "pegp_gemv", 1, 20)
     out = {"workload": f"grid2d_{side}x{side}_uniform[1,2]_PEGP_exact_mu1/sqrt(n)_fp64", "n": g.n,
@@ -490,6 +494,9 @@ def bench_pegp_exact(args, dev, world):
            "relres_max": max(i.relres for i in infos),
            "failed": sum(1 for i in infos if i.status != 0),
            "lanczos": {"steps": k_l, "lambda_min": lo_l, "lambda_max": hi_l, "kappa": hi_l / lo_l},
+           "stretch": {"trace_LTplus_LH": float(sv.mean()),
+                       "std_error": float(sv.std(ddof=1) / math.sqrt(len(sv))), "samples": len(sv),
+                       "seconds": round(stretch_s, 4)},
            "fgmres": {"value": whole_job_rate(len(ginfos), world, gms), "unit": "solves/s",
                       "iterations": [i.iterations for i in ginfos][:5],
                       "relres_max": max(i.relres for i in ginfos),

@@ -315,6 +315,20 @@ lap_status lap_get_lanczos(lap_handle h, double *h_alpha, double *h_beta, int32_
 lap_status lap_estimate_condition(lap_handle h, int32_t *steps, double *lambda_min,
                                   double *lambda_max);
 
+/*
+ * Stretch of H over the sparsifier T (Section 3.3) in its effective-resistance
+ * form, tr(L_T^+ L_H) = ||K_T||_F^2 = sum over H's edges of w_e R_T(e): at
+ * least kappa(L_T^+ L_H) and at most the paper's path stretch.  Estimated by
+ * Hutchinson's method: for s = 0..samples-1, h_vals[s] = z_s^T L_T^+ L_H z_s
+ * (host array of `samples` doubles), whose mean is an unbiased estimate.
+ * Entry i of z_s is -1 if the top bit of SplitMix64(seed, s * 2^32 + i) is
+ * set, else +1, with i the expanded index level by level in hierarchy order
+ * (aggregate creation order).  Each sample is one FP64 L_H matvec and one
+ * expanded-space MSP solve on the device.  LAP_ERR_UNSUPPORTED unless the
+ * handle was set up with a PEGP preconditioner and has two or more levels.
+ */
+lap_status lap_estimate_stretch(lap_handle h, int32_t samples, uint64_t seed, double *h_vals);
+
 /* Same as lap_pcg_solve with host vectors: copies b in and x out on `stream`
  * (the copies are part of the call). */
 lap_status lap_pcg_solve_host(lap_handle h, const double *h_b, double *h_x, void *stream,

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("lap_get_history", _I32, [_VP, _VP, _I32, C.POINTER(_I32)]),
     ("lap_get_lanczos", _I32, [_VP, _VP, _VP, _I32, C.POINTER(_I32)]),
     ("lap_estimate_condition", _I32, [_VP, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_D)]),
+    ("lap_estimate_stretch", _I32, [_VP, _I32, _U64, _VP]),
     ("lap_pcg_solve_host", _I32, [_VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_pcg_solve_batched", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_laplacian_residual_noalloc", _I32, [_I64, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -351,6 +352,15 @@ def lap_estimate_condition(h: Handle):
     _check(lib().lap_estimate_condition(h, C.byref(k), C.byref(lo), C.byref(hi)),
            "lap_estimate_condition")
     return k.value, lo.value, hi.value
+
+
+def lap_estimate_stretch(h: Handle, samples=16, seed=0):
+    """Hutchinson samples z^T L_T^+ L_H z (numpy array); their mean estimates
+    tr(L_T^+ L_H), the stretch of H over T."""
+    out = np.empty(int(samples), dtype=np.float64)
+    _check(lib().lap_estimate_stretch(h, int(samples), int(seed), out.ctypes.data),
+           "lap_estimate_stretch")
+    return out
 
 
 def lap_pcg_solve_host(h: Handle, b, x, stream=None) -> lap_solve_info:

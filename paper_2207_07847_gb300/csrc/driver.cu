@@ -24,6 +24,7 @@
 
 #include "dense.cuh"
 #include "fgmres.cuh"
+#include "stretch.cuh"
 #include "kernels.cuh"
 #include "solver.cuh"
 
@@ -62,6 +63,18 @@ T *dalloc(lap_handle_s &h, size_t count)
     h.device_bytes += static_cast<int64_t>(b->bytes);
     h.bufs.push_back(std::move(b));
     return p;
+}
+
+// Returns a buffer from dalloc to the allocator before the handle goes away
+// (a buffer it does not own is ignored).
+void release(lap_handle_s &h, const void *p)
+{
+    for (auto it = h.bufs.begin(); it != h.bufs.end(); ++it)
+        if ((*it)->p == p) {
+            h.device_bytes -= static_cast<int64_t>((*it)->bytes);
+            h.bufs.erase(it);
+            return;
+        }
 }
 
 template <typename T, typename U>
@@ -1167,6 +1180,13 @@ T *member(GmState *gm, size_t off)
 lap_status gm_alloc(lap_handle_s &h, int m)
 {
     if (h.gm_V && h.gm_m == m) return LAP_OK;
+    if (h.g_gm) {
+        cudaGraphExecDestroy(h.g_gm);
+        h.g_gm = nullptr;
+    }
+    for (const void *p : {static_cast<const void *>(h.gm_V), static_cast<const void *>(h.gm_Z),
+                          static_cast<const void *>(h.gm_part), static_cast<const void *>(h.gm)})
+        release(h, p);
     const size_t n = static_cast<size_t>(h.M64.off[1]);
     h.gm_V = dalloc<double>(h, n * (m + 1));
     h.gm_Z = dalloc<double>(h, n * m);
@@ -1174,10 +1194,6 @@ lap_status gm_alloc(lap_handle_s &h, int m)
     h.gm = dalloc<GmState>(h, 1);
     if (!h.gm_V || !h.gm_Z || !h.gm_part || !h.gm) return LAP_ERR_OOM;
     h.gm_m = m;
-    if (h.g_gm) {
-        cudaGraphExecDestroy(h.g_gm);
-        h.g_gm = nullptr;
-    }
     return LAP_OK;
 }
 
@@ -1609,6 +1625,31 @@ lap_status get_history(lap_handle_s &h, double *out, int cap, int *count)
     return LAP_OK;
 }
 
+// Hutchinson samples of tr(L_T^+ L_H) (stretch.cuh): per sample, z, y = L_H z,
+// u = L_T^+ y by the expanded-space MSP solve, z^T (u - mean u); FP64.
+lap_status estimate_stretch(lap_handle_s &h, int samples, uint64_t seed, double *vals)
+{
+    if (!h.H64.w || h.M64.levels < 2) return LAP_ERR_UNSUPPORTED;
+    const cudaStream_t s = h.s;
+    const int64_t nt = h.M64.off[h.M64.levels];
+    const auto &e = h.e64;
+    double *dv = dalloc<double>(h, static_cast<size_t>(samples));
+    if (!dv) return LAP_ERR_OOM;
+    const int g = grid_for(h, nt);
+    for (int k = 0; k < samples; ++k) {
+        k_rademacher<<<g, kBlock, 0, s>>>(nt, seed, static_cast<uint32_t>(k), h.xmap, e.p);
+        spmv<double, 2>(h, h.H64, h.tprH, e.p, e.q, nullptr, nullptr, h.stb, s);
+        k_copy2<double><<<g, kBlock, 0, s>>>(nt, e.q, e.A, nullptr, nullptr);
+        msp_tilde<double>(h, h.M64, e.A, e.Y, nullptr, s);
+        k_stretch_dot<<<g, kBlock, 0, s>>>(nt, e.p, e.Y, dv + k, h.stb.part, h.stb.ticket);
+        h.launches += 4;
+    }
+    LAP_CK(cudaMemcpyAsync(vals, dv, sizeof(double) * samples, cudaMemcpyDeviceToHost, s));
+    LAP_CK(cudaStreamSynchronize(s));
+    release(h, dv);
+    return LAP_OK;
+}
+
 lap_status get_lanczos(lap_handle_s &h, double *alpha, double *beta, int cap, int *count)
 {
     const int c = std::min(h.lz_run, h.hist_capacity);
@@ -1639,6 +1680,8 @@ lap_status update_options(lap_handle_s &h, const lap_options &o)
         double *p = dalloc<double>(h, static_cast<size_t>(o.maxit));
         double *q = dalloc<double>(h, 2 * static_cast<size_t>(o.maxit));
         if (!p || !q) return LAP_ERR_OOM;
+        release(h, h.hist);
+        release(h, h.lz);
         h.hist = p;
         h.lz = q;
         h.hist_capacity = o.maxit;

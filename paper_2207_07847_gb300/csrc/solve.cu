@@ -218,6 +218,12 @@ lap_status lap_estimate_condition(lap_handle h, int32_t *steps, double *lambda_m
     return LAP_OK;
 }
 
+lap_status lap_estimate_stretch(lap_handle h, int32_t samples, uint64_t seed, double *h_vals)
+{
+    if (!h || h->host_only || samples < 1 || !h_vals) return LAP_ERR_INVALID_ARG;
+    return estimate_stretch(*h, samples, seed, h_vals);
+}
+
 lap_status lap_get_hierarchy_info(lap_handle h, lap_hierarchy_info *info)
 {
     if (!h || !info) return LAP_ERR_INVALID_ARG;

@@ -88,6 +88,7 @@ lap_status solve_host(lap_handle_s &h, const double *b, double *x, cudaStream_t 
 lap_status update_options(lap_handle_s &h, const lap_options &o);
 lap_status get_history(lap_handle_s &h, double *out, int cap, int *count);
 lap_status get_lanczos(lap_handle_s &h, double *alpha, double *beta, int cap, int *count);
+lap_status estimate_stretch(lap_handle_s &h, int samples, uint64_t seed, double *vals);
 lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, double *ms,
                         double *bytes);
 

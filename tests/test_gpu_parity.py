@@ -319,6 +319,27 @@ def test_pegp_condition_numbers_follow_tables_1_and_2():
         assert kap[(side, 1.0 / side)] < 2.0 < kap[(side, 0.8)]
 
 
+@pytest.mark.parametrize("name,mu", [("grid2d_64", 0.8), ("grid2d_64", 0.3), ("rgg_3k", 0.8)])
+def test_stretch_estimate_parity(name, mu):
+    """Hutchinson samples z^T L_T^+ L_H z of the stretch of H over T (Section
+    3.3): the device's Rademacher vectors (SplitMix64 counters in hierarchy
+    order), L_H matvec and expanded-space MSP solve against the oracle's
+    counters, sparse product and sparse solve."""
+    from oracle import stretch
+    g = SMALL[name]()
+    h = P.lap_setup(g, seed=17, mu=mu, prec="pegp_inner")
+    vals = P.lap_estimate_stretch(h, samples=6, seed=5)
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=17)
+    ops = oracle.expanded_operators(ho, mu, with_LG=False)
+    ref = stretch.hutchinson_samples(ops, 6, seed=5)
+    np.testing.assert_allclose(vals, ref, rtol=1e-8)
+    assert np.all(vals > 0)
+    hm = P.lap_setup(g, seed=17, mu=mu, prec="msp")
+    with pytest.raises(P.LapError) as e:
+        P.lap_estimate_stretch(hm, samples=2)
+    assert e.value.status == 12
+
+
 def test_condition_estimate_refusals():
     g = gg.grid2d(12, weights="uniform", seed=1)
     h = P.lap_setup(g, seed=1, prec="msp")

@@ -332,7 +332,11 @@ def test_stretch_estimate_parity(name, mu):
     ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=17)
     ops = oracle.expanded_operators(ho, mu, with_LG=False)
     ref = stretch.hutchinson_samples(ops, 6, seed=5)
-    np.testing.assert_allclose(vals, ref, rtol=1e-8)
+    # the samples are dominated by effective resistances across the coarse
+    # levels, whose weights scale as mu^(2(k-1)): the device's elimination and
+    # the oracle's pivoted sparse LU of L_T agree to its conditioning (1.6e-8
+    # measured at mu = 0.3), so 1e-7
+    np.testing.assert_allclose(vals, ref, rtol=1e-7)
     assert np.all(vals > 0)
     hm = P.lap_setup(g, seed=17, mu=mu, prec="msp")
     with pytest.raises(P.LapError) as e:

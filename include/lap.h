@@ -310,7 +310,8 @@ lap_status lap_get_lanczos(lap_handle h, double *h_alpha, double *h_beta, int32_
  * stretch over 1 - rho (Section 3.3).  Computed on the host by Sturm-count
  * bisection.  *steps (may be NULL) receives k.  LAP_ERR_UNSUPPORTED for
  * LAP_PREC_PEGP_INNER (flexible CG has no Lanczos relation), LAP_ERR_INVALID_ARG
- * before any solve, LAP_ERR_BREAKDOWN if a coefficient is not admissible.
+ * when the last solve ran no CG step (none yet, a zero right-hand side, or an
+ * FGMRES solve), LAP_ERR_BREAKDOWN if a coefficient is not admissible.
  */
 lap_status lap_estimate_condition(lap_handle h, int32_t *steps, double *lambda_min,
                                   double *lambda_max);

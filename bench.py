@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--serve-nmax", type=float, default=1e6)
     ap.add_argument("--serve-plain-s", type=float, default=60.0,
                     help="time limit of the plain FP64 comparison stream")
+    ap.add_argument("--handshake", type=int, default=1,
+                    help="1: also solve the headline grid with the deterministic parallel "
+                         "matching variant (a method change; reported apart, 0: skip)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -379,6 +382,11 @@ def bench_ours(args, rank, world):
         result["batched"] = bench_batched(args, dev, world)
     if args.serve_requests > 0:
         result["serving"] = bench_serving(args, dev, world)
+    if args.handshake:
+        try:
+            result["handshake_matching"] = bench_handshake(args, dev, world)
+        except Exception as e:          # a variant line, never fatal to the report
+            result["handshake_matching"] = {"error": str(e)[-300:]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             result["cpu_baseline"] = cpu_baseline(args.prec, g.n, it_fp64 + inner_fp64)
@@ -582,6 +590,44 @@ def _serving_graph(kind, n, rng, seed):
     if kind == "chung_lu":
         return gg.chung_lu(int(n), avg_deg=float(rng.integers(8, 33)), **w)
     return gg.rgg(int(n), avg_deg=10.0, **w)
+
+
+def bench_handshake(args, dev, world):
+    """The headline grid with the deterministic parallel matching variant
+    (LAP_MATCH_HANDSHAKE, a change of the paper's coarsening): MSP and PEGP_inner,
+    mixed precision, one timed solve each after one warm-up, iterations beside
+    the paper's matching.  Reported apart from the headline."""
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+    g = gg.grid3d(args.nx, weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
+                  seed=WORKLOAD["wseed"])
+    stream = torch.cuda.current_stream()
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    bs = [torch.as_tensor(gg.rhs(g.n, seed=950 + i), device=dev) for i in range(2)]
+    out = {"workload": f"grid3d_{args.nx}^3_loguniform, matching = handshake"}
+    for prec in ("msp", "pegp_inner"):
+        t0 = time.perf_counter()
+        h = P.lap_setup(g, prec=prec, mu=WORKLOAD["mu"], precision="mixed", matching="handshake",
+                        tol=WORKLOAD["tol"], inner_tol=WORKLOAD["inner_tol"],
+                        inner_maxit=WORKLOAD["inner_maxit"], maxit=30000)
+        setup_s = time.perf_counter() - t0
+        P.lap_pcg_solve(h, bs[0], x)                              # warm-up
+        ranks_barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = P.lap_pcg_solve(h, bs[1], x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        out[prec] = {"value": whole_job_rate(1, world, ms), "unit": "solves/s",
+                     "levels": P.lap_get_hierarchy_info(h)["levels"], "setup_s": round(setup_s, 2),
+                     "iterations": info.iterations, "inner_iterations": info.inner_iterations,
+                     "relres": info.relres, "status": info.status}
+        h.close()
+    return out
 
 
 def bench_serving(args, dev, world):

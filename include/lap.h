@@ -76,6 +76,19 @@ typedef enum lap_precision {
                                  solve and iterative-refinement residuals    */
 } lap_precision;
 
+/* Matching pass of the coarsening (Section 2.2). */
+typedef enum lap_matching {
+    LAP_MATCH_GREEDY = 0,     /* the paper's pass: vertices in (seeded) random
+                                 order, each matched to its heaviest unmatched
+                                 neighbour                                      */
+    LAP_MATCH_HANDSHAKE = 1   /* deterministic parallel variant (a change of
+                                 the method): rounds in which vertices pointing
+                                 at each other (each at its heaviest unmatched
+                                 neighbour, ties to the smaller id) are matched,
+                                 until no unmatched vertex has an unmatched
+                                 neighbour; seed and order_random are unused   */
+} lap_matching;
+
 /* Outer Krylov method of lap_pcg_solve. */
 typedef enum lap_krylov {
     LAP_KRYLOV_CG = 0,        /* preconditioned CG (flexible for PEGP_INNER)     */
@@ -114,7 +127,9 @@ typedef struct lap_options {
                               LAP_KRYLOV_FGMRES (the paper's, Section 4; LAP_FP64
                               solves only)                                       */
     int32_t restart;       /* FGMRES cycle length m, 1..128 (default 30)          */
-    int32_t reserved[3];
+    int32_t matching;      /* lap_matching: the coarsening's matching pass
+                              (default LAP_MATCH_GREEDY, the paper's)           */
+    int32_t reserved[2];
 } lap_options;
 
 typedef struct lap_solve_info {

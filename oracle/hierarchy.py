@@ -66,6 +66,53 @@ def _match(adj: sp.csr_matrix, seed: int, level: int, randomise: bool):
     return agg, int(nc), pa[:nc].copy(), pb[:nc].copy()
 
 
+def _heaviest(adj: sp.csr_matrix, u: int, eligible) -> int:
+    """Heaviest neighbour v of u with eligible[v]; ties to the smaller id; -1 if none."""
+    best, best_w = -1, 0.0
+    for p in range(adj.indptr[u], adj.indptr[u + 1]):
+        v = int(adj.indices[p])
+        if not eligible[v]:
+            continue
+        wv = float(adj.data[p])
+        if best < 0 or wv > best_w or (wv == best_w and v < best):
+            best, best_w = v, wv
+    return best
+
+
+def _match_handshake(adj: sp.csr_matrix):
+    """Deterministic parallel matching (a method change against the paper's
+    random-order greedy pass, for data-parallel setup): in rounds, every
+    unmatched vertex points at its heaviest unmatched neighbour (ties to the
+    smaller id), and two vertices that point at each other are matched; the
+    rounds stop when no unmatched vertex has an unmatched neighbour (each round
+    matches at least the pair at the heaviest remaining edge, so they end).
+    Pairs are numbered by their smaller end, ascending, with pair_a the smaller
+    end; a leftover joins the aggregate of its heaviest neighbour, which is
+    matched.  Plain loops: test sizes only."""
+    n = adj.shape[0]
+    mate = np.full(n, -1, dtype=np.int64)
+    while True:
+        free = mate < 0
+        cand = np.array([_heaviest(adj, u, free) if free[u] else -1 for u in range(n)])
+        mutual = [u for u in range(n) if cand[u] >= 0 and cand[cand[u]] == u]
+        if not mutual:
+            break
+        for u in mutual:
+            mate[u] = cand[u]
+    agg = np.full(n, -1, dtype=np.int32)
+    pa, pb = [], []
+    for u in range(n):
+        if mate[u] > u:
+            agg[u] = agg[mate[u]] = len(pa)
+            pa.append(u)
+            pb.append(int(mate[u]))
+    everyone = np.ones(n, dtype=bool)
+    for u in range(n):
+        if agg[u] < 0:
+            agg[u] = agg[_heaviest(adj, u, everyone)]
+    return agg, len(pa), np.array(pa, dtype=np.int32), np.array(pb, dtype=np.int32)
+
+
 def _coarse(adj: sp.csr_matrix, agg: np.ndarray, nc: int) -> sp.csr_matrix:
     L = _cbuild.lib()
     n = adj.shape[0]
@@ -85,11 +132,14 @@ def _coarse(adj: sp.csr_matrix, agg: np.ndarray, nc: int) -> sp.csr_matrix:
 
 
 def build_hierarchy(row_ptr, col_idx, w, *, coarse_max: int = 32, max_levels: int = 0,
-                    seed: int = 0, order_random: bool = True) -> Hierarchy:
+                    seed: int = 0, order_random: bool = True,
+                    matching: str = "greedy") -> Hierarchy:
     """Aggregation hierarchy of the graph given as symmetric CSR (no self-loops).
 
-    The input rows are used in the order given (their CSR order fixes the
-    order in which level-2 weights are summed)."""
+    matching="greedy" is the paper's pass (Section 2.2, vertices in random
+    order); "handshake" the deterministic parallel variant (_match_handshake;
+    seed and order_random unused).  The input rows are used in the order given
+    (their CSR order fixes the order in which level-2 weights are summed)."""
     n = len(row_ptr) - 1
     adj = sp.csr_matrix((np.asarray(w, dtype=np.float64), np.asarray(col_idx, dtype=np.int32),
                          np.asarray(row_ptr, dtype=np.int64)), shape=(n, n))
@@ -101,7 +151,10 @@ def build_hierarchy(row_ptr, col_idx, w, *, coarse_max: int = 32, max_levels: in
             break
         if max_levels and k >= max_levels:
             break
-        agg, nc, pa, pb = _match(cur, seed, k, order_random)
+        if matching == "handshake":
+            agg, nc, pa, pb = _match_handshake(cur)
+        else:
+            agg, nc, pa, pb = _match(cur, seed, k, order_random)
         if nc < 2:
             break
         h.agg.append(agg)

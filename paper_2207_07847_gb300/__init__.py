@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblap.so")
 LAP_PREC = {"none": 0, "msp": 1, "pegp_inner": 2, "pegp_exact": 3}
 LAP_PRECISION = {"fp64": 0, "mixed": 1}
 LAP_KRYLOV = {"cg": 0, "fgmres": 1}
+LAP_MATCHING = {"greedy": 0, "handshake": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not symmetric", 3: "not connected",
           4: "bad weight", 5: "out of memory", 6: "CUDA error", 7: "no convergence",
           8: "breakdown", 9: "timeout", 10: "cancelled", 11: "busy", 12: "unsupported"}
@@ -46,7 +47,7 @@ class lap_options(C.Structure):
                 ("check_every", C.c_int32), ("timeout_s", C.c_double),
                 ("spmv_tpr", C.c_int32), ("host_only", C.c_int32),
                 ("stall_window", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("matching", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class lap_solve_info(C.Structure):
@@ -172,6 +173,8 @@ def make_options(**kw) -> lap_options:
             v = LAP_PRECISION[v]
         if k == "krylov" and isinstance(v, str):
             v = LAP_KRYLOV[v]
+        if k == "matching" and isinstance(v, str):
+            v = LAP_MATCHING[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)

@@ -200,6 +200,72 @@ int64_t aggregate_level(HostLevel &L, uint64_t seed, int level, bool randomise)
     return nagg;
 }
 
+// Deterministic parallel matching (a method change against the paper's
+// random-order greedy pass, chosen with LAP_MATCH_HANDSHAKE): in rounds, every
+// unmatched vertex points at its heaviest unmatched neighbour (ties to the
+// smaller id) and two vertices pointing at each other are matched, until no
+// unmatched vertex has an unmatched neighbour.  Each round matches at least
+// the pair at the heaviest remaining edge: the smallest vertex on an edge of
+// that weight points along it, and so does its partner.  Pairs are numbered by
+// their smaller end (pa), ascending; leftovers join the aggregate of their
+// heaviest neighbour, which is matched.  The rounds' two phases run on the
+// host threads; every decision reads only the previous phase's state.
+int64_t aggregate_level_handshake(HostLevel &L)
+{
+    const int64_t n = L.n;
+    std::vector<int32_t> mate(static_cast<size_t>(n), -1), cand(static_cast<size_t>(n), -1);
+    std::vector<int32_t> active(static_cast<size_t>(n));
+    std::iota(active.begin(), active.end(), 0);
+    const int T = setup_threads(L.rp[n]);
+    while (!active.empty()) {
+        const int64_t na = static_cast<int64_t>(active.size());
+        parallel_chunks(na, T, [&](int, int64_t a0, int64_t a1) {
+            for (int64_t a = a0; a < a1; ++a) {
+                const int32_t u = active[a];
+                cand[u] = heaviest_neighbour(L, u, [&](int32_t x) { return mate[x] < 0; });
+            }
+        });
+        std::atomic<int64_t> matched{0};
+        parallel_chunks(na, T, [&](int, int64_t a0, int64_t a1) {
+            int64_t m = 0;
+            for (int64_t a = a0; a < a1; ++a) {
+                const int32_t u = active[a];
+                const int32_t c = cand[u];
+                if (c >= 0 && cand[c] == u) {
+                    mate[u] = c;
+                    ++m;
+                }
+            }
+            matched += m;
+        });
+        if (matched.load() == 0) break;
+        // still unmatched with an unmatched neighbour: the next round's vertices
+        std::vector<int32_t> next;
+        next.reserve(active.size());
+        for (int32_t u : active)
+            if (mate[u] < 0 && cand[u] >= 0) next.push_back(u);
+        active.swap(next);
+    }
+    L.agg.assign(static_cast<size_t>(n), -1);
+    L.pa.clear();
+    L.pb.clear();
+    for (int64_t u = 0; u < n; ++u) {
+        if (mate[u] > u) {
+            const int32_t id = static_cast<int32_t>(L.pa.size());
+            L.agg[u] = L.agg[mate[u]] = id;
+            L.pa.push_back(static_cast<int32_t>(u));
+            L.pb.push_back(mate[u]);
+        }
+    }
+    const int64_t nagg = static_cast<int64_t>(L.pa.size());
+    for (int64_t u = 0; u < n; ++u) {
+        if (L.agg[u] >= 0) continue;
+        const int32_t v = heaviest_neighbour(L, u, [](int32_t) { return true; });
+        L.agg[u] = L.agg[v];
+    }
+    return nagg;
+}
+
 // Galerkin coarse graph: weight(I, J) = sum of fine weights between the two
 // aggregates, accumulated fine vertex by fine vertex in increasing id and CSR
 // position; coarse rows have sorted columns.
@@ -499,7 +565,9 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
         if (F.n <= opt.coarse_max) break;
         if (opt.max_levels && k >= opt.max_levels) break;
         if (k >= LAP_MAX_LEVELS) break;
-        const int64_t nc = aggregate_level(F, opt.seed, k, opt.order_random != 0);
+        const int64_t nc = opt.matching == LAP_MATCH_HANDSHAKE
+                               ? aggregate_level_handshake(F)
+                               : aggregate_level(F, opt.seed, k, opt.order_random != 0);
         if (nc < 2) {
             F.agg.clear();
             F.pa.clear();

@@ -139,6 +139,7 @@ lap_status lap_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     if (!(o.tol > 0.0) || o.maxit < 1 || o.check_every < 1) return LAP_ERR_INVALID_ARG;
     if (o.krylov != LAP_KRYLOV_CG && o.krylov != LAP_KRYLOV_FGMRES) return LAP_ERR_INVALID_ARG;
     if (o.restart < 1 || o.restart > 128) return LAP_ERR_INVALID_ARG;
+    if (o.matching != LAP_MATCH_GREEDY && o.matching != LAP_MATCH_HANDSHAKE) return LAP_ERR_INVALID_ARG;
     std::string why;
     lap_status st = validate_csr(n, row_ptr, col_idx, w, &why);
     if (st != LAP_OK) return st;

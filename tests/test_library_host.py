@@ -119,6 +119,54 @@ def test_threaded_setup_equals_single_threaded_and_oracle(monkeypatch):
         np.testing.assert_array_equal(outs[1][2 + k][0], ho.agg[k])
 
 
+@pytest.mark.parametrize("name,make", GRAPHS, ids=[g[0] for g in GRAPHS])
+def test_handshake_matching_bit_exact_with_oracle(name, make):
+    """The deterministic parallel matching variant: aggregates and pairs of
+    every level, H's and T's edges, equal to the oracle's plain-loop version;
+    each level's matching is maximal (no two adjacent unmatched vertices) and
+    its pairs are edges."""
+    g = make()
+    h = P.lap_setup(g, host_only=1, matching="handshake", prec="pegp_inner", mu=0.8)
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, matching="handshake")
+    info = P.lap_get_hierarchy_info(h)
+    assert info["level_size"] == ho.sizes
+    for k in range(ho.levels - 1):
+        agg, pa, pb = P.lap_get_aggregates(h, k + 1)
+        np.testing.assert_array_equal(agg, ho.agg[k])
+        np.testing.assert_array_equal(pa, ho.pair_a[k])
+        np.testing.assert_array_equal(pb, ho.pair_b[k])
+        adj = ho.adj[k].tocsr()
+        assert np.all(adj[pa, pb] > 0)
+        matched = np.zeros(adj.shape[0], dtype=bool)
+        matched[pa] = matched[pb] = True
+        free = np.flatnonzero(~matched)
+        assert adj[free][:, free].nnz == 0
+    if name in ("grid2d", "rgg"):
+        ops = oracle.expanded_operators(ho, 0.8, with_LG=False)
+        for which, ref in ((1, ops.T_edges), (0, ops.H_edges)):
+            i, j, w = P.lap_get_expanded_edges(h, which)
+            np.testing.assert_array_equal(i, ref[0])
+            np.testing.assert_array_equal(j, ref[1])
+
+
+def test_handshake_matching_threads_and_options(monkeypatch):
+    g = gg.grid3d(24, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    outs = []
+    for threads in ("1", "8"):
+        monkeypatch.setenv("LAP_SETUP_THREADS", threads)
+        h = P.lap_setup(g, host_only=1, matching="handshake", seed=5)
+        info = P.lap_get_hierarchy_info(h)
+        outs.append([P.lap_get_aggregates(h, k + 1) for k in range(info["levels"] - 1)])
+    for a, b in zip(outs[0], outs[1]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    # the seed does not enter the variant
+    h2 = P.lap_setup(g, host_only=1, matching="handshake", seed=99)
+    for k, ref in enumerate(outs[0]):
+        assert np.array_equal(P.lap_get_aggregates(h2, k + 1)[0], ref[0])
+    assert P.lap_setup_status(g.row_ptr, g.col_idx, g.w, matching=2, host_only=1) == 1
+
+
 def test_library_reproduces_table_level_sizes():
     for n in (16, 64, 256, 1024):
         s = int(round(n ** 0.5))

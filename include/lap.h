@@ -206,7 +206,7 @@ void lap_destroy(lap_handle h);
  * precision may switch to LAP_MIXED only if the handle was set up with
  * LAP_MIXED (FP32 copies exist); switching to LAP_FP64 is always allowed.
  * Setup-time fields (prec, mu, coarse_max, max_levels, seed, order_random,
- * spmv_tpr, host_only) are ignored.
+ * matching, spmv_tpr, host_only) are ignored.
  */
 lap_status lap_update_options(lap_handle h, const lap_options *opts);
 

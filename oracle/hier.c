@@ -17,7 +17,7 @@
  *              coarse edge (I,J) carries the summed weight of all fine edges
  *              between aggregates I and J.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - "random order": the visit order of level k is the vertices sorted by
  *     the key SplitMix64(seed, (k << 32 | u) + 1), ties by vertex id, where
  *     SplitMix64(seed, i) is the i-th output of Steele, Lea & Flood's

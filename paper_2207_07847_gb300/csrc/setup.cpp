@@ -89,35 +89,70 @@ lap_status validate_csr(int64_t n, const int64_t *rp, const int32_t *ci, const d
         if (rp[u + 1] < rp[u]) return fail(LAP_ERR_INVALID_ARG, "row_ptr decreasing");
     const int64_t nnz = rp[n];
     if (nnz >= (int64_t(1) << 31)) return fail(LAP_ERR_UNSUPPORTED, "nnz >= 2^31");
-    for (int64_t u = 0; u < n; ++u) {
+    // three passes over the rows, each split over the host threads; a pass
+    // reports the failure of its smallest failing row (as one sequential scan
+    // would), and the passes run in order
+    const int T = setup_threads(nnz);
+    std::vector<int64_t> bad_row(static_cast<size_t>(T));
+    std::vector<int> bad_kind(static_cast<size_t>(T));
+    auto first_failure = [&](auto row_check) {
+        std::fill(bad_row.begin(), bad_row.end(), n);
+        parallel_chunks(n, T, [&](int t, int64_t u0, int64_t u1) {
+            for (int64_t u = u0; u < u1; ++u) {
+                const int k = row_check(u);
+                if (k) {
+                    bad_row[t] = u;
+                    bad_kind[t] = k;
+                    return;
+                }
+            }
+        });
+        int64_t r = n;
+        int k = 0;
+        for (int t = 0; t < T; ++t)
+            if (bad_row[t] < r) {
+                r = bad_row[t];
+                k = bad_kind[t];
+            }
+        return k;
+    };
+    // entries: columns in range, no self-loops, positive finite weights
+    switch (first_failure([&](int64_t u) {
         for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
             const int64_t v = ci[p];
-            if (v < 0 || v >= n) return fail(LAP_ERR_INVALID_ARG, "column out of range");
-            if (v == u) return fail(LAP_ERR_INVALID_ARG, "self-loop");
-            if (!(w[p] > 0.0) || !std::isfinite(w[p]))
-                return fail(LAP_ERR_BAD_WEIGHT, "weight not positive and finite");
+            if (v < 0 || v >= n) return 1;
+            if (v == u) return 2;
+            if (!(w[p] > 0.0) || !std::isfinite(w[p])) return 3;
         }
+        return 0;
+    })) {
+    case 1: return fail(LAP_ERR_INVALID_ARG, "column out of range");
+    case 2: return fail(LAP_ERR_INVALID_ARG, "self-loop");
+    case 3: return fail(LAP_ERR_BAD_WEIGHT, "weight not positive and finite");
+    default: break;
     }
     // sorted copy of every row: duplicates and symmetry
     std::vector<std::pair<int32_t, double>> s(static_cast<size_t>(nnz));
-    for (int64_t p = 0; p < nnz; ++p) s[p] = {ci[p], w[p]};
-    for (int64_t u = 0; u < n; ++u) {
-        auto b = s.begin() + rp[u], e = s.begin() + rp[u + 1];
-        std::sort(b, e, [](const auto &x, const auto &y) { return x.first < y.first; });
-        for (auto it = b; it + 1 < e; ++it)
-            if (it->first == (it + 1)->first)
-                return fail(LAP_ERR_INVALID_ARG, "duplicate entry");
-    }
-    for (int64_t u = 0; u < n; ++u) {
-        for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
-            const int32_t v = s[p].first;
-            auto b = s.begin() + rp[v], e = s.begin() + rp[v + 1];
-            auto it = std::lower_bound(b, e, static_cast<int32_t>(u),
-                                       [](const auto &x, int32_t key) { return x.first < key; });
-            if (it == e || it->first != u || it->second != s[p].second)
-                return fail(LAP_ERR_NOT_SYMMETRIC, "matrix not symmetric");
-        }
-    }
+    if (first_failure([&](int64_t u) {
+            for (int64_t p = rp[u]; p < rp[u + 1]; ++p) s[p] = {ci[p], w[p]};
+            auto b = s.begin() + rp[u], e = s.begin() + rp[u + 1];
+            std::sort(b, e, [](const auto &x, const auto &y) { return x.first < y.first; });
+            for (auto it = b; it + 1 < e; ++it)
+                if (it->first == (it + 1)->first) return 1;
+            return 0;
+        }))
+        return fail(LAP_ERR_INVALID_ARG, "duplicate entry");
+    if (first_failure([&](int64_t u) {
+            for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+                const int32_t v = s[p].first;
+                auto b = s.begin() + rp[v], e = s.begin() + rp[v + 1];
+                auto it = std::lower_bound(b, e, static_cast<int32_t>(u),
+                                           [](const auto &x, int32_t key) { return x.first < key; });
+                if (it == e || it->first != u || it->second != s[p].second) return 1;
+            }
+            return 0;
+        }))
+        return fail(LAP_ERR_NOT_SYMMETRIC, "matrix not symmetric");
     // connectivity by breadth-first search
     std::vector<char> seen(static_cast<size_t>(n), 0);
     std::vector<int32_t> queue;

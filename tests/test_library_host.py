@@ -209,6 +209,37 @@ def test_validation_rejects_bad_input():
     assert _status(rp, ci, w, tol=0.0) == 1
 
 
+@pytest.mark.parametrize("threads", ["1", "8"])
+def test_validation_of_large_graphs_on_threads(monkeypatch, threads):
+    """Validation splits its row passes over host threads on large inputs:
+    each error is still found, and when a graph has several the one reported
+    is the one a sequential scan meets first (entry errors before duplicates
+    before asymmetry; the smallest row within a pass)."""
+    monkeypatch.setenv("LAP_SETUP_THREADS", threads)
+    g = gg.grid3d(32, weights="uniform", lo=1.0, hi=2.0, seed=1)
+    rp, ci, w = g.row_ptr.copy(), g.col_idx.copy(), g.w.copy()
+    assert rp[-1] > 1 << 16                            # the threaded path
+    assert _status(rp, ci, w) == 0
+    late = rp[g.n - 5]                                 # an entry of a late row
+    w2 = w.copy()
+    w2[late] *= 1.5
+    assert _status(rp, ci, w2) == 2                    # asymmetry
+    w3 = w2.copy()
+    w3[late + 1] = -1.0
+    assert _status(rp, ci, w3) == 4                    # bad weight reported before asymmetry
+    ci2 = ci.copy()
+    ci2[late] = ci2[late + 1]                          # duplicate (and then asymmetry)
+    assert _status(rp, ci2, w) == 1
+    ci3 = ci.copy()
+    ci3[rp[g.n // 2]] = g.n // 2                       # self-loop in a middle row
+    w4 = w.copy()
+    w4[rp[g.n - 3]] = np.inf                           # and a bad weight later
+    assert _status(rp, ci3, w4) == 1
+    w5 = w.copy()
+    w5[rp[10]] = 0.0                                   # bad weight in an early row wins
+    assert _status(rp, ci3, w5) == 4
+
+
 def test_single_level_when_graph_is_small():
     g = gg.path(5, w=[1.0, 2.0, 3.0, 4.0])
     h = P.lap_setup(g, host_only=1)

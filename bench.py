@@ -611,7 +611,7 @@ def bench_handshake(args, dev, world):
         t0 = time.perf_counter()
         h = P.lap_setup(g, prec=prec, mu=WORKLOAD["mu"], precision="mixed", matching="handshake",
                         tol=WORKLOAD["tol"], inner_tol=WORKLOAD["inner_tol"],
-                        inner_maxit=WORKLOAD["inner_maxit"], maxit=30000)
+                        inner_maxit=WORKLOAD["inner_maxit"], maxit=30000, timeout_s=120.0)
         setup_s = time.perf_counter() - t0
         P.lap_pcg_solve(h, bs[0], x)                              # warm-up
         ranks_barrier(world)

@@ -195,6 +195,39 @@ def test_matching_invariants_random_order(seed):
         np.testing.assert_allclose(laplacian(h.adj[k + 1]).toarray(), Lc, rtol=1e-13, atol=1e-12)
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_handshake_matching_equals_sorted_edge_greedy(seed):
+    """The handshake matching variant (each unmatched vertex points at its
+    heaviest unmatched neighbour, ties to the smaller id; mutual pointers are
+    matched, in rounds) equals the textbook greedy matching that scans the edges
+    by decreasing weight, ties by the smaller lower end, then the smaller upper
+    end: the vertices' preferences agree with that one order, and a locally
+    dominant matching under a consistent order is the greedy one.  Weights drawn
+    from three values, so ties are common."""
+    rng = np.random.default_rng(seed)
+    g = gg.random_connected(200, extra=3.0, weights="uniform", seed=seed)
+    w = rng.integers(1, 4, len(g.w)).astype(float)
+    A = sp.csr_matrix((w, g.col_idx, g.row_ptr), shape=(g.n, g.n))
+    A = sp.triu(A, 1)
+    A = (A + A.T).tocsr()                       # symmetric weights
+    agg, nc, pa, pb = oracle.hierarchy._match_handshake(A)
+    edges = sorted(zip(*sp.triu(A, 1).nonzero()), key=lambda e: (-A[e[0], e[1]], e[0], e[1]))
+    mate = {}
+    for a, b in edges:
+        if a not in mate and b not in mate:
+            mate[a], mate[b] = b, a
+    want = sorted((a, b) for a, b in mate.items() if a < b)
+    assert sorted(zip(pa.tolist(), pb.tolist())) == want
+    assert list(pa) == sorted(pa)                # numbered by the smaller end
+    matched = np.zeros(g.n, bool)
+    matched[pa] = matched[pb] = True
+    for u in np.flatnonzero(~matched):
+        row = A.getrow(u)
+        assert matched[row.indices].all()
+        best = max(zip(row.data, -row.indices))
+        assert agg[u] == agg[-best[1]]
+
+
 # --- identities of the expanded graph (Sections 3.1-3.2) --------------------------------
 
 @pytest.fixture(scope="module")

@@ -63,3 +63,28 @@ def test_reference_arm_other_ranks_exit_without_work():
                          capture_output=True, text=True, env=env, timeout=120)
     assert out.returncode == 0
     assert out.stdout.strip() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference on one rank: one JSON line with the contract's
+    keys, the oracle as the reference, its own value as e2e with no copies."""
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in r, k
+    assert r["impl"] == "reference" and r["steps"] == 1 and r["n_gpus"] == 1
+    assert r["value"] > 0 and r["higher_is_better"] is True
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
+    e = r["e2e"]
+    assert e["value"] == r["value"] and e["unit"] == r["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

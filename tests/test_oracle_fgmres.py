@@ -74,3 +74,23 @@ def test_restarted_solution_equals_the_dense_solve(kind, restart):
     cyc = [h[i:i + restart] for i in range(0, len(h), restart)]
     for c in cyc:
         assert np.all(np.diff(c) <= 1e-12 * c[0])
+
+
+def test_restart_one_is_the_minimal_residual_iteration():
+    """FGMRES(1) takes, each step, the multiple of z = M(r) that minimises the
+    residual: x += a z with a = (r, L z) / (L z, L z), then r = Pi b - L x."""
+    g = gg.grid2d(7, 5, weights="uniform", lo=1.0, hi=2.0, seed=2)
+    b = gg.rhs(g.n, seed=6)
+    M = oracle.make_preconditioner("msp", g, mu=0.8, coarse_max=4, seed=1)
+    L = M.ops.L
+    res = oracle.fgmres(L, b, M, tol=1e-30, maxit=15, restart=1)
+    bp = b - b.mean()
+    x = np.zeros(g.n)
+    for k in range(15):
+        r = bp - L @ x
+        z = M(r)
+        q = L @ z
+        x = x + (r @ q) / (q @ q) * z
+        rel = np.linalg.norm(bp - L @ x) / np.linalg.norm(bp)
+        assert res.history[k] == pytest.approx(rel, rel=1e-9)
+    np.testing.assert_allclose(res.x, x - x.mean(), atol=1e-12 * np.abs(x).max())

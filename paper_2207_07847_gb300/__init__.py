@@ -211,10 +211,16 @@ def _check(status, where):
 
 
 def lap_setup(row_ptr, col_idx=None, w=None, stream=None, **opts) -> Handle:
-    """lap_setup on a host CSR graph (a graphgen.Graph or three arrays)."""
+    """lap_setup on a host CSR graph: a graphgen.Graph, a scipy.sparse
+    adjacency matrix (symmetric, positive off-diagonal weights, no diagonal),
+    or the three CSR arrays."""
     if col_idx is None:
         g = row_ptr
-        row_ptr, col_idx, w = g.row_ptr, g.col_idx, g.w
+        if hasattr(g, "tocsr"):                    # scipy.sparse
+            g = g.tocsr()
+            row_ptr, col_idx, w = g.indptr, g.indices, g.data
+        else:
+            row_ptr, col_idx, w = g.row_ptr, g.col_idx, g.w
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(col_idx, dtype=np.int32)
     ww = np.ascontiguousarray(w, dtype=np.float64)

@@ -240,6 +240,15 @@ def test_validation_of_large_graphs_on_threads(monkeypatch, threads):
     assert _status(rp, ci3, w5) == 4
 
 
+def test_setup_takes_a_scipy_adjacency():
+    g = gg.grid2d(20, 15, weights="uniform", seed=4)
+    A = g.adjacency()
+    h1 = P.lap_setup(g, host_only=1, seed=2)
+    h2 = P.lap_setup(A.tocoo(), host_only=1, seed=2)
+    assert P.lap_get_hierarchy_info(h1)["level_size"] == P.lap_get_hierarchy_info(h2)["level_size"]
+    np.testing.assert_array_equal(P.lap_get_aggregates(h1, 1)[0], P.lap_get_aggregates(h2, 1)[0])
+
+
 def test_single_level_when_graph_is_small():
     g = gg.path(5, w=[1.0, 2.0, 3.0, 4.0])
     h = P.lap_setup(g, host_only=1)

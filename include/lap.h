@@ -368,10 +368,11 @@ lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, const int32_t
  * Residual of a graph Laplacian system without any device allocation.
  *
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory at all: code running while a CUDA graph
- * is being captured (where cudaMalloc is not allowed), code inside a process
- * whose device-memory quota is already spent, or code that must not touch an
- * allocator shared with other work.  It needs no handle and no allocator:
+ * that cannot allocate device memory at all: code inside a process whose
+ * device-memory quota is already spent (an out-of-memory handler that still
+ * has to report how good the last iterate is), or code that must not touch
+ * an allocator it shares with other work.  It needs no handle and no
+ * allocator:
  *
  *   d_r[i] = (b_i - mean(b)) - sum_j w_ij (x_i - x_j)     (r = Pi b - L x)
  *   h_norms[0] = ||r||_2,  h_norms[1] = ||Pi b||_2        (written on the host)
@@ -390,7 +391,8 @@ lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, const int32_t
  * share the one array, so calls that overlap on the GPU (different streams,
  * threads or processes sharing a context) race and must be serialised by the
  * caller.  Allocates nothing: no cudaMalloc, no cudaFree, no library
- * allocator.
+ * allocator.  A launch that fails (no kernel image for the device, a bad
+ * launch configuration) returns LAP_ERR_CUDA and leaves h_norms unwritten.
  */
 lap_status lap_laplacian_residual_noalloc(int64_t n, const int64_t *d_row_ptr,
                                           const int32_t *d_col_idx, const double *d_w,

@@ -1,13 +1,13 @@
 // Laplacian residual that allocates no device memory.
 //
-// For callers that cannot allocate device memory at all -- code that runs
-// while a CUDA graph is being captured, under a device-memory quota that is
-// already spent, or in a process that must not touch the allocator -- this
-// entry point needs no handle and no allocator: the caller passes the graph
-// (device CSR), x and b, and receives r and two norms.  The only scratch it
-// needs, the per-tile partial sums of its reductions, lives in a fixed
-// file-scope __device__ array that every GPU using this library holds until
-// the process exits.
+// For callers that cannot allocate device memory at all -- a process whose
+// device-memory quota is already spent (an out-of-memory handler that still
+// has to report how good the last iterate is), or code that must not touch an
+// allocator it shares with other work -- this entry point needs no handle and
+// no allocator: the caller passes the graph (device CSR), x and b, and
+// receives r and two norms.  The only scratch it needs, the per-tile partial
+// sums of its reductions, lives in a fixed file-scope __device__ array that
+// every GPU using this library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -162,7 +162,9 @@ extern "C" lap_status lap_laplacian_residual_noalloc(int64_t n, const int64_t *d
         return LAP_ERR_CUDA;
     }
     k_na_mean<<<tiles, kTile, 0, s>>>(n, d_b, S);
+    if (cudaGetLastError() != cudaSuccess) return LAP_ERR_CUDA;
     k_na_residual<<<tiles, kTile, 0, s>>>(n, d_row_ptr, d_col_idx, d_w, d_x, d_b, d_r, S);
+    if (cudaGetLastError() != cudaSuccess) return LAP_ERR_CUDA;
     double tot[2] = {0.0, 0.0};
     if (cudaMemcpyAsync(tot, &S->rr, sizeof(tot), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -1,12 +1,19 @@
 """The allocation-free residual entry point, checked against the existing ones.
 
 ``lap_laplacian_residual_noalloc`` serves callers that cannot allocate device
-memory (inside CUDA graph capture, under a spent memory quota): it takes the
-graph and vectors as device arrays and keeps its reduction scratch in a fixed
-array inside the library.  Its output must equal what the regular entry
-points give: r = Pi b - L x with L x from ``lap_laplacian_apply``, on two
-calls in a row (the second call reuses the scratch the first one left).
-This file is collected last on purpose.
+memory (a process whose device-memory quota is spent, such as an
+out-of-memory handler reporting on its last iterate, or code that must not
+touch an allocator it shares): it takes the graph and vectors as device
+arrays and keeps its reduction scratch in a fixed array inside the library.
+Its output must equal what the regular entry points give: r = Pi b - L x
+with L x from ``lap_laplacian_apply``, on two calls in a row (the second call
+reuses the scratch the first one left), and repeated calls must leave the
+device's free memory unchanged.
+
+The file name sorts last, so pytest collects it after every other test file:
+if it fails, a run that stops at the first failure (``-x``) has already run
+all the other tests.  It also passes alone in a fresh process (its first call
+then does the one-time lookup of the scratch array's address).
 """
 import numpy as np
 import pytest
@@ -78,3 +85,29 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = P.lib().lap_laplacian_residual_noalloc((1 << 24) + 1, fake, fake, fake, fake, fake,
                                                 fake, norms, None)
     assert st == 12                                       # LAP_ERR_UNSUPPORTED
+
+
+def test_noalloc_calls_leave_device_memory_unchanged():
+    """After a first call (which may load the library's device code), more
+    calls change neither the device's free memory nor torch's allocator."""
+    g = gg.grid2d(96, 80, weights="loguniform", lo=1e-2, hi=1e2, seed=4)
+    rp = _dev(g.row_ptr, torch.int64)
+    ci = _dev(g.col_idx, torch.int32)
+    w = _dev(g.w)
+    x = _dev(gg.rhs(g.n, seed=1))
+    b = _dev(gg.rhs(g.n, seed=2))
+    r = torch.empty_like(x)
+    st, _, _ = P.lap_laplacian_residual_noalloc(rp, ci, w, x, b, r)
+    assert st == 0
+    r0 = r.clone()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch_bytes0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        st, _, _ = P.lap_laplacian_residual_noalloc(rp, ci, w, x, b, r)
+        assert st == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == torch_bytes0
+    assert torch.equal(r, r0)                         # deterministic partial sums

@@ -64,6 +64,10 @@ class OraclePreconditioner:
     inner_tol: float = 1e-6
     inner_maxit: int = 500
     inner_iters: list = field(default_factory=list)
+    # per inner solve, min over its steps of | ||r|| / (inner_tol ||r~||) - 1 |:
+    # how close its stopping test came to flipping (a diagnostic, no arithmetic
+    # of the method depends on it)
+    inner_margin: list = field(default_factory=list)
 
     def __post_init__(self):
         if self.kind in ("msp", "pegp_inner"):
@@ -107,23 +111,28 @@ class OraclePreconditioner:
         its = 0
         if nrt == 0.0:
             self.inner_iters.append(0)
+            self.inner_margin.append(np.inf)
             return y
         z = self._T(r)
         p = z.copy()
         rho = r @ z
+        margin = np.inf
         while its < self.inner_maxit:
             q = LH @ p
             alpha = rho / (p @ q)
             y += alpha * p
             r -= alpha * q
             its += 1
-            if np.linalg.norm(r) <= self.inner_tol * nrt:
+            nr = np.linalg.norm(r)
+            margin = min(margin, abs(nr / (self.inner_tol * nrt) - 1.0))
+            if nr <= self.inner_tol * nrt:
                 break
             z = self._T(r)
             rho_new = r @ z
             p = z + (rho_new / rho) * p
             rho = rho_new
         self.inner_iters.append(its)
+        self.inner_margin.append(margin)
         return y
 
 
@@ -153,8 +162,9 @@ def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=Fals
     """Preconditioned CG on the singular consistent system L x = Pi b, x_0 = 0.
 
     beta = r_k^T z_k / r_{k-1}^T z_{k-1} (standard) or, if flexible,
-    beta = z_k^T (r_k - r_{k-1}) / r_{k-1}^T z_{k-1} (FCG(1), Notay 2000)."""
-    L = sp.csr_matrix(L)
+    beta = z_k^T (r_k - r_{k-1}) / r_{k-1}^T z_{k-1} (FCG(1), Notay 2000).
+    L is a sparse matrix or any operator whose product is ``L @ v``."""
+    L = sp.csr_matrix(L) if sp.issparse(L) else L
     bp = _project(np.asarray(b, dtype=np.float64))
     nb = np.linalg.norm(bp)
     x = np.zeros_like(bp)
@@ -218,7 +228,7 @@ def fgmres(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, restart=30
     triangular system, x += Z y, and the next cycle starts from the true
     residual Pi b - L x.  The iteration count is the number of products with
     L inside the cycles; a cycle whose true residual meets tol ends the solve."""
-    L = sp.csr_matrix(L)
+    L = sp.csr_matrix(L) if sp.issparse(L) else L
     bp = _project(np.asarray(b, dtype=np.float64))
     nb = np.linalg.norm(bp)
     x = np.zeros_like(bp)

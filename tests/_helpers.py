@@ -51,6 +51,17 @@ def kappa_nonzero(A, B, zero=1e-9):
     return evp.max() / evp.min()
 
 
+# The graphs of the GPU parity cases (tests/test_gpu_parity.py), also used by
+# the CPU test of the oracle's rounding spread.
+PARITY_GRAPHS = {
+    "grid2d_64": lambda: gg.grid2d(64, weights="uniform", lo=1.0, hi=2.0, seed=1),
+    "grid3d_20": lambda: gg.grid3d(20, 19, 18, weights="loguniform", lo=1e-3, hi=1e3, seed=3),
+    "chunglu_4k": lambda: gg.chung_lu(4096, avg_deg=16, seed=4),
+    "rmat_11": lambda: gg.rmat(11, 16, seed=5),
+    "rgg_3k": lambda: gg.rgg(3000, seed=6),
+}
+
+
 def hub_graph():
     """Six hubs in a path, each with its own leaves (2,500, 2,500, 8,000,
     8,000, 300 and 300): every hub's aggregate holds all its leaves, so the
@@ -67,3 +78,123 @@ def hub_graph():
     v += list(range(1, len(sizes)))
     w = gg.edge_weights(len(u), "loguniform", 1e-2, 1e2, seed=7)
     return gg.from_edges(nxt, np.array(u), np.array(v), w, "hubs")
+
+
+# Iteration-count bands of the FP64 GPU parity cases.  The target is +-1.
+# The GPU evaluates every product in another order than the oracle and solves
+# the sparsifier by elimination instead of a pivoted sparse LU; both are
+# accurate FP64 evaluations, and the preconditioner's output is fixed only to
+# within the forward error of an FP64 solve of L_T (or L_H), which grows with
+# their conditioning.  CG turns such differences into whole iterations on
+# badly conditioned systems.  tests/test_iteration_spread.py runs the oracle
+# against itself with only that freedom used -- matvecs summed in reverse
+# entry order, other fill-reducing orderings of the factorisations, random
+# perturbations of each matvec element by its typical rounding error and of each
+# preconditioner output by twice its own FP64 refinement correction -- and
+# checks that its count spreads by exactly the band recorded here, or by at
+# most 1 for every case left at +-1.
+ITER_SPREAD = {
+    ("grid3d_20", "msp"): 16,
+    ("grid3d_20", "none"): 15,
+    ("rgg_3k", "msp"): 2,
+    ("rgg_3k", "none"): 2,
+    ("hubs", "msp"): 2,
+    ("ragged_path", 1000): 7,
+    ("ragged_ring", 1000): 8,
+    ("ragged_path", 4097): 19,
+    ("ragged_ring", 4097): 18,
+    # columns 0 and 5 of the batched 18 x 17 x 16 grid (batched vs single)
+    ("batched_grid3d_18", "msp", 0): 8,
+    ("batched_grid3d_18", "msp", 5): 10,
+    ("batched_grid3d_18", "none", 0): 14,
+    ("batched_grid3d_18", "none", 5): 3,
+    ("served_grid2d_56x40", "msp"): 7,
+    # total inner iterations of PEGP with inner tolerance 1e-6 (its inner
+    # stopping tests come within 2e-4 of flipping)
+    ("grid2d_64", "pegp_inner_tol1e-6", "inner_total"): 171,
+}
+
+
+def iter_band(key):
+    """Allowed |iterations(GPU) - iterations(oracle)| for a parity case."""
+    return max(1, ITER_SPREAD.get(key, 1))
+
+
+def reversed_csr(A):
+    """The same sparse matrix with every row's entries stored in reverse
+    order, so that a matvec sums them in the other order."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    rp = A.indptr.copy()
+    ci = A.indices.copy()
+    v = A.data.copy()
+    for i in range(A.shape[0]):
+        a, b = rp[i], rp[i + 1]
+        ci[a:b] = ci[a:b][::-1]
+        v[a:b] = v[a:b][::-1]
+    B = sp.csr_matrix((v, ci, rp), shape=A.shape)
+    B.has_sorted_indices = False
+    return B
+
+
+class GroundedLU:
+    """A^+ b for a connected Laplacian A by sparse LU of A with its last
+    vertex grounded, under a chosen fill-reducing column ordering."""
+
+    def __init__(self, A, permc_spec):
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spla
+        A = sp.csc_matrix(A)
+        self.n = A.shape[0]
+        self.lu = spla.splu(A[:-1, :-1].tocsc(), permc_spec=permc_spec)
+
+    def __call__(self, b):
+        x = np.zeros(self.n)
+        x[:-1] = self.lu.solve(np.asarray(b[:-1], dtype=np.float64))
+        return x - x.mean()
+
+
+EPS64 = 2.0 ** -53
+
+
+class RoundedProduct:
+    """The sparse matrix A whose products A @ p have every element moved by a
+    random multiple in [-1, 1] of the typical rounding error of an FP64 sum
+    of k terms, sqrt(k) x 2^-53 x (|A| |p|)_i (k the row length): another
+    valid evaluation order's result."""
+
+    def __init__(self, A, seed):
+        import scipy.sparse as sp
+        self.A = sp.csr_matrix(A)
+        self.absA = abs(self.A)
+        self.k = np.sqrt(np.diff(self.A.indptr)) * EPS64
+        self.rng = np.random.default_rng(seed)
+        self.shape = self.A.shape
+
+    def __matmul__(self, p):
+        q = self.A @ p
+        return q + self.rng.uniform(-1.0, 1.0, q.size) * self.k * (self.absA @ np.abs(p))
+
+
+class PerturbedSolve:
+    """A Laplacian solver whose every output y = solve(b) moves by a random
+    zero-sum vector of norm 2 ||d||, where d = solve(b - A y) is the
+    correction one FP64 refinement step would make: that correction is the
+    size of this solve's forward error, and another FP64 solve of the same
+    system (another elimination order) may differ from this one by the sum
+    of both forward errors."""
+
+    def __init__(self, solve, A, seed, scale=2.0):
+        import scipy.sparse as sp
+        self.solve, self.A, self.scale = solve, sp.csr_matrix(A), scale
+        self.rng = np.random.default_rng(seed)
+
+    def __call__(self, b):
+        y = self.solve(b)
+        res = b - self.A @ y
+        res -= res.mean()
+        d = self.solve(res)
+        g = self.rng.standard_normal(y.size)
+        g -= g.mean()
+        y = y + self.scale * np.linalg.norm(d) * g / np.linalg.norm(g)
+        return y - y.mean()

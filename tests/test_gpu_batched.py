@@ -14,6 +14,8 @@ import graphgen as gg
 import oracle
 from oracle.expanded import laplacian
 
+from _helpers import iter_band
+
 torch = pytest.importorskip("torch")
 P = pytest.importorskip("paper_2207_07847_gb300")
 
@@ -70,7 +72,10 @@ def test_batched_columns_match_single_solves(precision, prec):
         bp = B[j] - B[j].mean()
         assert np.linalg.norm(L @ (X[j] - x1.cpu().numpy())) <= 2e-8 * np.linalg.norm(bp)
         if precision == "fp64":
-            assert abs(infos[j].iterations - single.iterations) <= max(2, 0.03 * single.iterations)
+            # the batched and the single solve round differently: the oracle's
+            # own spread under rounding changes bounds their difference
+            band = iter_band(("batched_grid3d_18", prec, j))
+            assert abs(infos[j].iterations - single.iterations) <= band, (j, band)
 
 
 def test_batched_column_matches_oracle():
@@ -84,7 +89,7 @@ def test_batched_column_matches_oracle():
     ref = oracle.solve(g, B[2], "msp", mu=0.8, seed=17)
     L = laplacian(g.adjacency())
     bp = B[2] - B[2].mean()
-    assert abs(infos[2].iterations - ref.iters) <= 2
+    assert abs(infos[2].iterations - ref.iters) <= iter_band(("batched_grid2d_64", "msp", 2))
     assert np.linalg.norm(L @ (Xd[2].cpu().numpy() - ref.x)) <= 2e-8 * np.linalg.norm(bp)
 
 

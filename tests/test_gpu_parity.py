@@ -9,10 +9,11 @@ tensors and compares with the oracle on the same seeded inputs.  Tolerances:
 * FP64 solves: the recurrence residual histories agree to 1e-9 relative over
   the first 12 iterations (the same iteration, step by step, before rounding
   differences of the two summation orders grow; measured divergence starts
-  between iterations 14 and 150); iteration counts agree to +-1, or to 3% of
-  the count, since CG's loss of orthogonality amplifies rounding over hundreds
-  of iterations on badly conditioned problems; both true relative residuals
-  are <= 1e-8, so ||L (x_gpu - x_oracle)|| <= 2e-8 ||Pi b||;
+  between iterations 14 and 150); iteration counts agree to +-1, except where
+  the oracle's own count moves by more than 1 when only its rounding changes
+  (``_helpers.ITER_SPREAD``, measured by tests/test_iteration_spread.py):
+  there the band is that spread; both true relative residuals are <= 1e-8,
+  so ||L (x_gpu - x_oracle)|| <= 2e-8 ||Pi b||;
 * mixed precision: true relative residual <= 1e-8 and the solution within the
   error that residual allows of the oracle's.
 """
@@ -23,7 +24,7 @@ import graphgen as gg
 import oracle
 from oracle.expanded import laplacian
 
-from _helpers import hub_graph
+from _helpers import PARITY_GRAPHS, hub_graph, iter_band
 
 torch = pytest.importorskip("torch")
 P = pytest.importorskip("paper_2207_07847_gb300")
@@ -57,13 +58,7 @@ def solve_gpu(h, b):
     return x, info
 
 
-SMALL = {
-    "grid2d_64": lambda: gg.grid2d(64, weights="uniform", lo=1.0, hi=2.0, seed=1),
-    "grid3d_20": lambda: gg.grid3d(20, 19, 18, weights="loguniform", lo=1e-3, hi=1e3, seed=3),
-    "chunglu_4k": lambda: gg.chung_lu(4096, avg_deg=16, seed=4),
-    "rmat_11": lambda: gg.rmat(11, 16, seed=5),
-    "rgg_3k": lambda: gg.rgg(3000, seed=6),
-}
+SMALL = PARITY_GRAPHS
 
 
 @pytest.fixture(scope="module", params=list(SMALL))
@@ -165,14 +160,14 @@ def _oracle_solve(g, b, kind, mu, **kw):
     return oracle.solve(g, b, kind, mu=mu, seed=17, **kw)
 
 
-def _check_trajectory(h, info, ref, head=12, rtol=1e-9):
+def _check_trajectory(h, info, ref, key, head=12, rtol=1e-9):
     hist = P.lap_get_history(h)
     oh = np.array(ref.history)
     m = min(head, len(hist), len(oh))
     assert len(hist) == info.iterations
     np.testing.assert_allclose(hist[:m], oh[:m], rtol=rtol, atol=1e-13)
-    band = max(1, int(round(0.03 * ref.iters)))
-    assert abs(info.iterations - ref.iters) <= band, (info.iterations, ref.iters)
+    band = iter_band(key)
+    assert abs(info.iterations - ref.iters) <= band, (key, info.iterations, ref.iters, band)
 
 
 @pytest.mark.parametrize("kind", ["msp", "none"])
@@ -183,7 +178,7 @@ def test_fp64_solve_parity(case, kind):
     x, info = solve_gpu(h, dev(b))
     ref = _oracle_solve(g, b, kind, 0.8, maxit=3000)
     assert info.status == 0 and ref.converged
-    _check_trajectory(h, info, ref)
+    _check_trajectory(h, info, ref, (name, kind))
     xg = host(x)
     bp = b - b.mean()
     assert np.linalg.norm(bp - ops.L @ xg) <= 1e-8 * np.linalg.norm(bp)
@@ -202,13 +197,55 @@ def test_fp64_pegp_inner_parity():
     ref = oracle.pcg(M.ops.L, b, M, flexible=True)
     assert info.status == 0 and ref.converged
     # inner solves stop at 1e-6, so the preconditioners agree to about that
-    _check_trajectory(h, info, ref, head=5, rtol=1e-5)
-    assert abs(info.inner_iterations - sum(M.inner_iters)) <= max(2, 0.03 * sum(M.inner_iters))
+    _check_trajectory(h, info, ref, ("grid2d_64", "pegp_inner_tol1e-6"), head=5, rtol=1e-5)
+    assert abs(info.inner_iterations - sum(M.inner_iters)) <= iter_band(
+        ("grid2d_64", "pegp_inner_tol1e-6", "inner_total"))
     L = laplacian(g.adjacency())
     bp = b - b.mean()
     xg = host(x)
     assert np.linalg.norm(bp - L @ xg) <= 1e-8 * np.linalg.norm(bp)
     assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * np.linalg.norm(bp)
+
+
+@pytest.mark.parametrize("side", [16, 20])
+def test_pegp_inner_at_the_benchmark_settings(side):
+    """The headline preconditioner with the benchmark's inner settings (inner
+    CG on L_H preconditioned by MSP, cap 12, inner tolerance 0.1, mu = 0.8) on
+    log-uniform 3D grids.  Every inner solve of the oracle stops at the cap
+    with its stopping test far from flipping, so the GPU runs the same
+    preconditioner: the outer residuals agree step by step over the first 30
+    iterations to 1e-9 (the oracle against itself with only its rounding
+    changed agrees to 4e-12 at step 30 and to 1e-9 up to step 57), the counts
+    within the oracle's own spread, each inner solve 12 iterations.  The mixed
+    precision run of the same system meets the tolerance and its solution's
+    error against the oracle's is the one the residuals allow."""
+    g = gg.grid3d(side, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    b = gg.rhs(g.n, seed=8)
+    M = oracle.make_preconditioner("pegp_inner", g, mu=0.8, seed=17, inner_tol=0.1,
+                                   inner_maxit=12)
+    ref = oracle.pcg(M.ops.L, b, M, flexible=True, maxit=3000)
+    assert ref.converged and set(M.inner_iters) == {12} and min(M.inner_margin) > 0.1
+    h = P.lap_setup(g, seed=17, mu=0.8, prec="pegp_inner", inner_tol=0.1, inner_maxit=12,
+                    maxit=3000)
+    x, info = solve_gpu(h, dev(b))
+    assert info.status == 0, info.as_dict()
+    _check_trajectory(h, info, ref, (f"grid3d_{side}", "pegp_inner_bench"), head=30)
+    assert info.inner_iterations % 12 == 0
+    assert abs(info.inner_iterations - sum(M.inner_iters)) <= 12 * iter_band(
+        (f"grid3d_{side}", "pegp_inner_bench"))
+    L = M.ops.L
+    bp = b - b.mean()
+    nb = np.linalg.norm(bp)
+    xg = host(x)
+    assert np.linalg.norm(bp - L @ xg) <= 1e-8 * nb
+    assert np.linalg.norm(L @ (xg - ref.x)) <= 2e-8 * nb
+    hm = P.lap_setup(g, seed=17, mu=0.8, prec="pegp_inner", inner_tol=0.1, inner_maxit=12,
+                     maxit=5000, precision="mixed")
+    xm, infm = solve_gpu(hm, dev(b))
+    assert infm.status == 0 and infm.relres <= 1e-8, infm.as_dict()
+    xm = host(xm)
+    assert np.linalg.norm(bp - L @ xm) <= 1e-8 * nb
+    assert np.linalg.norm(L @ (xm - ref.x)) <= 2e-8 * nb
 
 
 @pytest.mark.parametrize("mu", [1 / 64, 0.3, 0.8])
@@ -223,8 +260,7 @@ def test_fp64_pegp_exact_parity(mu):
     x, info = solve_gpu(h, dev(b))
     ref = _oracle_solve(g, b, "pegp_exact", mu)
     assert info.status == 0 and ref.converged
-    _check_trajectory(h, info, ref)
-    assert abs(info.iterations - ref.iters) <= 1
+    _check_trajectory(h, info, ref, ("grid2d_64", "pegp_exact", mu))
     L = laplacian(g.adjacency())
     bp = b - b.mean()
     xg = host(x)
@@ -395,7 +431,7 @@ def test_fgmres_parity(name):
     m = min(5 if inexact else 12, len(hist), len(ref.history))
     np.testing.assert_allclose(hist[:m], ref.history[:m], rtol=1e-5 if inexact else 1e-9,
                                atol=1e-13)
-    assert abs(info.iterations - ref.iters) <= max(1, int(round(0.03 * ref.iters)))
+    assert abs(info.iterations - ref.iters) <= iter_band((name, "fgmres", kind))
     assert abs(info.restarts - ref.restarts) <= 1
     L = laplacian(g.adjacency())
     bp = b - b.mean()
@@ -463,13 +499,14 @@ def test_single_level_graph_is_solved_directly():
 
 @pytest.mark.parametrize("n", [2, 3, 33, 65, 1000, 4097])
 def test_ragged_path_and_ring_sizes(n):
-    for g in (gg.path(n, w=np.linspace(1, 2, n - 1)), gg.ring(max(n, 5), 2, weights="uniform", seed=n)):
+    for gname, g in (("ragged_path", gg.path(n, w=np.linspace(1, 2, n - 1))),
+                     ("ragged_ring", gg.ring(max(n, 5), 2, weights="uniform", seed=n))):
         b = gg.rhs(g.n, seed=n)
         h = P.lap_setup(g, seed=17, coarse_max=2, maxit=5000)
         x, info = solve_gpu(h, dev(b))
         ref = _oracle_solve(g, b, "msp", 0.8, coarse_max=2, maxit=5000)
         assert info.status == 0 and ref.converged
-        _check_trajectory(h, info, ref)
+        _check_trajectory(h, info, ref, (gname, n))
         L = laplacian(g.adjacency())
         bp = b - b.mean()
         assert np.linalg.norm(bp - L @ host(x)) <= 1e-8 * np.linalg.norm(bp)
@@ -583,7 +620,11 @@ def test_hub_aggregates_and_oversized_tiles(precision):
     x, inf = solve_gpu(h, b)
     assert inf.status == 0, inf.as_dict()
     ref = oracle.solve(g, host(b), "msp", mu=0.8, seed=17)
-    assert abs(inf.iterations - ref.iters) <= max(2, round(0.03 * ref.iters)) or precision == "mixed"
+    # FP64: the iteration of the oracle, +-1 (its own count does not move
+    # under rounding here).  Mixed precision counts FP32 inner iterations over
+    # refinement steps: another iteration, whose count is not compared.
+    if precision == "fp64":
+        assert abs(inf.iterations - ref.iters) <= iter_band(("hubs", "msp")), (inf.iterations, ref.iters)
     L = laplacian(g.adjacency())
     bp = host(b) - host(b).mean()
     assert np.linalg.norm(L @ (host(x) - ref.x)) <= 2e-8 * np.linalg.norm(bp)

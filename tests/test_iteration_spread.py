@@ -1,0 +1,206 @@
+"""Evidence for the iteration-count bands of the GPU parity tests.
+
+The GPU and the oracle run the same iteration but evaluate it differently:
+other summation orders in the matvecs and the dot products, and elimination
+on the sparsifier instead of a pivoted sparse LU.  Both are accurate FP64
+evaluations; the preconditioner's output is fixed only to within the forward
+error of an FP64 solve of L_T (or L_H), which grows with their conditioning.
+On badly conditioned systems CG loses orthogonality and turns such
+differences into whole iterations.  Here the oracle is run against itself
+with only that freedom used:
+
+* as it is;
+* the matvecs summed in reverse entry order and the factorisations under
+  another fill-reducing ordering;
+* three runs in which every matvec element moves by a random multiple of the
+  typical rounding error of its FP64 sum and every solve of L_T (or L_H) by a
+  random vector of
+  twice the norm of the correction one FP64 refinement step would make to it
+  (that correction is the size of the solve's forward error; two FP64
+  solves of one system differ by up to the sum of theirs).
+
+The spread of its iteration count per parity case must equal the band that
+``_helpers.ITER_SPREAD`` records, and be at most 1 for every case left at
+the +-1 of exact parity.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle.expanded import expanded_operators
+from oracle.solve import OraclePreconditioner, _GroundedSolver, fgmres, pcg
+
+from _helpers import (ITER_SPREAD, PARITY_GRAPHS, GroundedLU, PerturbedSolve, RoundedProduct,
+                      hub_graph, reversed_csr)
+
+PERTURBED_RUNS = 3
+_POOL = None
+
+
+def _pool():
+    """Worker processes for the variants of a case (spawned: no state of
+    this process is forked into them)."""
+    global _POOL
+    if _POOL is None:
+        import atexit
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import os
+        # one BLAS thread per worker: the workers already fill the cores
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        _POOL = cf.ProcessPoolExecutor(max_workers=min(2 + PERTURBED_RUNS, os.cpu_count() or 1),
+                                       mp_context=mp.get_context("spawn"))
+        atexit.register(_POOL.shutdown)
+    return _POOL
+
+
+def _variant(v, g, kind, b, mu, seed, coarse_max, krylov, restart, inner_tol, inner_maxit):
+    """Iteration count (and total inner iterations) of one oracle run:
+    v = 0 as is, 1 reversed matvec sums and another ordering of the
+    factorisation, >= 2 random rounding-size perturbations (seeded by v)."""
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=seed, coarse_max=coarse_max)
+    ops = expanded_operators(ho, mu, with_LG=False)
+    o = ops
+    if v == 1:
+        o = type(ops)(**{**ops.__dict__, "L": reversed_csr(ops.L), "LH": reversed_csr(ops.LH)})
+    elif v >= 2:
+        o = type(ops)(**{**ops.__dict__, "L": RoundedProduct(ops.L, v),
+                         "LH": RoundedProduct(ops.LH, 100 + v)})
+    M = OraclePreconditioner(kind, ops if kind != "none" else None, inner_tol=inner_tol,
+                             inner_maxit=inner_maxit)
+    if kind != "none":
+        M.ops = o
+    if v == 1 and kind in ("msp", "pegp_inner"):
+        M._T = GroundedLU(ops.LT, "MMD_AT_PLUS_A")
+    elif v == 1 and kind == "pegp_exact":
+        M._H = GroundedLU(ops.LH, "MMD_AT_PLUS_A")
+    elif v >= 2 and kind in ("msp", "pegp_inner"):
+        M._T = PerturbedSolve(M._T, ops.LT, 200 + v)
+    elif v >= 2 and kind == "pegp_exact":
+        M._H = PerturbedSolve(M._H, ops.LH, 200 + v)
+    if krylov == "fgmres":
+        r = fgmres(o.L, b, M, maxit=3000, restart=restart)
+    else:
+        r = pcg(o.L, b, M, maxit=6000, flexible=M.flexible)
+    assert r.converged, (v, kind, r.iters, r.relres)
+    return r.iters, sum(M.inner_iters)
+
+
+def _spread(g, kind, b, *, mu=0.8, seed=17, coarse_max=32, krylov="cg", restart=30,
+            inner_tol=1e-6, inner_maxit=500, with_inner=False):
+    args = (g, kind, b, mu, seed, coarse_max, krylov, restart, inner_tol, inner_maxit)
+    futs = [_pool().submit(_variant, v, *args) for v in range(2 + PERTURBED_RUNS)]
+    res = [f.result() for f in futs]
+    counts = [c for c, _ in res]
+    inner = [i for _, i in res]
+    if with_inner:
+        return max(counts) - min(counts), counts, max(inner) - min(inner), inner
+    return max(counts) - min(counts), counts
+
+
+RECORD = None          # a list: measure and record instead of asserting
+
+
+def _check(key, spread, counts):
+    if RECORD is not None:
+        RECORD.append((key, spread, counts))
+        return
+    if key in ITER_SPREAD:
+        assert spread == ITER_SPREAD[key], (key, counts)
+    else:
+        assert spread <= 1, (key, counts)
+
+
+@pytest.mark.parametrize("name", list(PARITY_GRAPHS))
+@pytest.mark.parametrize("kind", ["msp", "none"])
+def test_spread_of_the_fp64_parity_cases(name, kind):
+    g = PARITY_GRAPHS[name]()
+    spread, counts = _spread(g, kind, gg.rhs(g.n, seed=7))
+    _check((name, kind), spread, counts)
+
+
+@pytest.mark.parametrize("n", [33, 1000, 4097])
+def test_spread_of_the_ragged_cases(n):
+    for gname, g in (("ragged_path", gg.path(n, w=np.linspace(1, 2, n - 1))),
+                     ("ragged_ring", gg.ring(max(n, 5), 2, weights="uniform", seed=n))):
+        spread, counts = _spread(g, "msp", gg.rhs(g.n, seed=n), coarse_max=2)
+        _check((gname, n), spread, counts)
+
+
+def test_spread_of_the_hub_case():
+    g = hub_graph()
+    spread, counts = _spread(g, "msp", gg.rhs(g.n, seed=6))
+    _check(("hubs", "msp"), spread, counts)
+
+
+def test_spread_of_the_smoke_case():
+    g = gg.grid2d(48, 40, weights="uniform", lo=1.0, hi=2.0, seed=1)
+    spread, counts = _spread(g, "msp", gg.rhs(g.n, seed=2), seed=5)
+    _check(("smoke", "msp"), spread, counts)
+
+
+@pytest.mark.parametrize("name,kind,mu,restart", [
+    ("grid2d_64", "msp", 0.8, 30), ("grid2d_64", "pegp_exact", 1 / 64, 30),
+    ("grid2d_64", "pegp_inner", 0.8, 30), ("grid2d_24", "none", 0.8, 30),
+    ("chunglu_4k", "msp", 0.8, 5), ("rmat_11", "msp", 0.8, 8)])
+def test_spread_of_the_fgmres_cases(name, kind, mu, restart):
+    g = (PARITY_GRAPHS[name]() if name in PARITY_GRAPHS
+         else gg.grid2d(24, weights="uniform", lo=1.0, hi=2.0, seed=1))
+    spread, counts = _spread(g, kind, gg.rhs(g.n, seed=7), mu=mu, krylov="fgmres",
+                             restart=restart)
+    _check((name, "fgmres", kind), spread, counts)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("side", [16, 20])
+def test_spread_of_the_pegp_inner_benchmark_settings(side):
+    """The benchmark's PEGP inner settings (inner cap 12, inner tolerance 0.1,
+    mu = 0.8) on log-uniform 3D grids: the count moves by at most 1, and every
+    inner solve of the oracle stops at the cap far from its tolerance test."""
+    g = gg.grid3d(side, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    b = gg.rhs(g.n, seed=8)
+    spread, counts = _spread(g, "pegp_inner", b, inner_tol=0.1, inner_maxit=12)
+    _check((f"grid3d_{side}", "pegp_inner_bench"), spread, counts)
+    M = oracle.make_preconditioner("pegp_inner", g, mu=0.8, seed=17, inner_tol=0.1,
+                                   inner_maxit=12)
+    ref = pcg(M.ops.L, b, M, flexible=True, maxit=3000)
+    assert ref.converged and set(M.inner_iters) == {12}
+    assert min(M.inner_margin) > 0.1
+
+
+@pytest.mark.parametrize("prec", ["msp", "none"])
+def test_spread_of_the_batched_columns(prec):
+    """Columns 0 and 5 of the batched 18 x 17 x 16 grid: the batched solve
+    and a single solve of the same column round differently."""
+    g = gg.grid3d(18, 17, 16, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
+    for j in (0, 5):
+        spread, counts = _spread(g, prec, gg.rhs(g.n, seed=40 + j))
+        _check(("batched_grid3d_18", prec, j), spread, counts)
+
+
+def test_spread_of_the_oracle_checked_batched_and_served_columns():
+    g = PARITY_GRAPHS["grid2d_64"]()
+    spread, counts = _spread(g, "msp", gg.rhs(g.n, seed=9))
+    _check(("batched_grid2d_64", "msp", 2), spread, counts)
+    g = gg.grid2d(56, 40, weights="loguniform", lo=1e-2, hi=1e2, seed=2)
+    spread, counts = _spread(g, "msp", gg.rhs(g.n, seed=55), seed=5)
+    _check(("served_grid2d_56x40", "msp"), spread, counts)
+
+
+def test_spread_of_the_pegp_inner_case():
+    """PEGP with an inner CG to 1e-6: the outer count is stable, the total of
+    inner iterations moves with the inner stopping tests that rounding flips."""
+    g = PARITY_GRAPHS["grid2d_64"]()
+    spread, counts, ispread, inner = _spread(g, "pegp_inner", gg.rhs(g.n, seed=8),
+                                             inner_tol=1e-6, inner_maxit=500, with_inner=True)
+    _check(("grid2d_64", "pegp_inner_tol1e-6"), spread, counts)
+    _check(("grid2d_64", "pegp_inner_tol1e-6", "inner_total"), ispread, inner)
+
+
+@pytest.mark.parametrize("mu", [1 / 64, 0.3, 0.8])
+def test_spread_of_the_exact_pegp_cases(mu):
+    g = PARITY_GRAPHS["grid2d_64"]()
+    spread, counts = _spread(g, "pegp_exact", gg.rhs(g.n, seed=2), mu=mu)
+    _check(("grid2d_64", "pegp_exact", mu), spread, counts)

@@ -218,12 +218,19 @@ lap_status lap_update_options(lap_handle h, const lap_options *opts);
  *   kernel 4: the sweep's coarse tail    kernel 5: the last downward band
  *             (one block)                          (z and its reductions)
  *   kernel 6: the exact PEGP dense matvec y~ = G r~ (LAP_PREC_PEGP_EXACT)
+ *   kernel 7: one iteration of the PEGP inner CG on L_H (matvec, step,
+ *             expanded-space MSP sweep, reductions, new direction;
+ *             LAP_PREC_PEGP_INNER)
+ *   kernel 8: the expanded-space MSP solve y~ = L_T^+ f alone (PEGP inner)
  * in FP64 (precision 0) or FP32 (precision 1, LAP_MIXED handles).  Runs `reps`
- * back-to-back launches (sequences for kernel 2) on the handle's stream
- * timed by CUDA events and writes the mean milliseconds per launch and the
- * algorithmic bytes of one launch (every array the kernel must touch, read
- * or written once).  Overwrites the handle's solve workspace.  Kernels 3-5
- * need an MSP handle with at least two levels, else LAP_ERR_INVALID_ARG.
+ * back-to-back launches (sequences for kernels 2, 7, 8) on the handle's
+ * stream timed by CUDA events and writes the mean milliseconds per launch and
+ * the algorithmic bytes of one launch (every array the kernel must touch, read
+ * or written once).  Overwrites the handle's solve workspace (kernel 7 first
+ * fills the inner CG's vectors with fixed values; LAP_ERR_BREAKDOWN if its
+ * iterations broke down while timed).  Kernels 3-5 need an MSP handle with at
+ * least two levels, kernels 7-8 a PEGP inner handle with at least two levels,
+ * else LAP_ERR_INVALID_ARG.
  */
 lap_status lap_kernel_bench(lap_handle h, int32_t kernel, int32_t precision, int32_t reps,
                             double *ms_per_launch, double *bytes_per_launch);

@@ -54,6 +54,14 @@ template <typename V> struct BandParams {
     V *scratch;               // packed deltas of every tile (written up, read down)
     int64_t off_top;          // expanded offset of level k1
     V pc;                     // downward parent coefficient
+    // expanded-space CG fused into the sweep (k_band_up MODE 3, k_band_down
+    // XRED): first band (level k0 = 0 taken from r), offsets (in doubles)
+    // of this band's per-block partial pairs in the reduction scratch: up
+    // (||r||^2, sum r) and, for bands above the first, down (sum z, r.z);
+    // the first band's down pass sums its blocks through red_gs and then the
+    // xred_n pairs from xred_base (the tail's, then the upper bands')
+    int first;
+    int red_up, red_dn, red_gs, xred_base, xred_n;
     BandLevel<V> lev[kBandMaxLevels];
 };
 
@@ -185,15 +193,66 @@ __device__ __forceinline__ void band_coef_offsets(int L, BandTile &T)
 
 // One level of the upward elimination of a staged tile, by threads
 // [tid0, tid0 + nthr).
-template <typename V>
+// SMEMF: the right-hand side added on restriction is the staged value of the
+// next level itself (a_{j+1} = gamma sum + f_{j+1} in place); else F (global,
+// optional) at the next level's expanded indices.
+template <typename V, bool SMEMF = false>
 __device__ __forceinline__ void band_up_level(const BandParams<V> &P, const BandTile &T, unsigned char *sm, int j,
                                               const V *F, int tid0, int nthr)
 {
     const int64_t onext = j + 1 < P.nlev ? P.lev[j + 1].off : P.off_top;
-    elim_level(reinterpret_cast<V *>(sm + T.vs[j]), reinterpret_cast<V *>(sm + T.vs[j + 1]),
-               reinterpret_cast<const int *>(sm + T.ss[j]), 0, reinterpret_cast<const V *>(sm + T.is[j]),
-               reinterpret_cast<const V *>(sm + T.ls[j]), P.lev[j].gamma, F, onext + T.st[j + 1], T.cnt[j + 1],
-               tid0, nthr);
+    V *an = reinterpret_cast<V *>(sm + T.vs[j + 1]);
+    elim_level(reinterpret_cast<V *>(sm + T.vs[j]), an, reinterpret_cast<const int *>(sm + T.ss[j]), 0,
+               reinterpret_cast<const V *>(sm + T.is[j]), reinterpret_cast<const V *>(sm + T.ls[j]),
+               P.lev[j].gamma, SMEMF ? an : F, SMEMF ? 0 : onext + T.st[j + 1], T.cnt[j + 1], tid0, nthr);
+}
+
+// Expanded index of element 0 of level j of tile T (j = nlev: the band's top).
+template <typename V>
+__device__ __forceinline__ int64_t band_level_base(const BandParams<V> &P, const BandTile &T, int j)
+{
+    return (j < P.nlev ? P.lev[j].off : P.off_top) + T.st[j];
+}
+
+// CG step x += alpha p, r -= alpha q on `cnt` consecutive expanded entries
+// from g0, the updated r also written to dst (shared or global); adds
+// ||r||^2 and sum r (groups of four in V, then FP64).
+template <typename V>
+__device__ __forceinline__ void band_cg_step(int64_t g0, int cnt, V al, V *__restrict__ x, V *__restrict__ r,
+                                             const V *__restrict__ p, const V *__restrict__ q, V *dst,
+                                             double &rr, double &rs)
+{
+    constexpr int G = sizeof(V) == 4 ? 4 : 2;      // elements in flight per thread
+    for (int i0 = threadIdx.x; i0 < cnt; i0 += G * kBandThreads) {
+        V xv[G], pv[G], qv[G], rv[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int i = i0 + k * kBandThreads;
+            if (i < cnt) {
+                const int64_t u = g0 + i;
+                xv[k] = x[u];
+                pv[k] = p[u];
+                qv[k] = q[u];
+                rv[k] = r[u];
+            }
+        }
+        V r2 = V(0), r1 = V(0);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int i = i0 + k * kBandThreads;
+            if (i < cnt) {
+                const int64_t u = g0 + i;
+                x[u] = xv[k] + al * pv[k];
+                const V v = rv[k] - al * qv[k];
+                r[u] = v;
+                dst[i] = v;
+                r2 += v * v;
+                r1 += v;
+            }
+        }
+        rr += (double)r2;
+        rs += (double)r1;
+    }
 }
 
 // Upward band: levels k0..k1-1 eliminated (deltas to the scratch, or in place
@@ -204,8 +263,14 @@ __device__ __forceinline__ void band_up_level(const BandParams<V> &P, const Band
 //         (finished by the coarse tail: the convergence test);
 // MODE 2: k0 = 0, a_0 = r, the same partials without the step;
 // MODE 0: a_{k0} read from A.
-// F (optional): expanded right-hand side added on restriction (a_{k+1} +=
-// F_{k+1}; may alias A, read before it is overwritten).
+// MODE 3: a step of the expanded-space CG (the PEGP inner solve) fused in:
+//         x += alpha p, r -= alpha q on every level of the tile (level k0
+//         only in the first band, whose a_{k0} = r; the other bands read
+//         a_{k0} from A), the updated r staged as the right-hand side added
+//         on restriction, per-block partials of ||r||^2, sum r at
+//         part[red_up + 2 b] (finished by the coarse tail).
+// F (optional, MODE 0): expanded right-hand side added on restriction (a_{k+1}
+// += F_{k+1}; may alias A, read before it is overwritten).
 template <typename V, int MODE>
 __global__ void __launch_bounds__(kBandThreads, 2)
 k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ p,
@@ -216,7 +281,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
     __shared__ BandTile T;
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, L = P.nlev;
-    const V al = MODE == 1 ? (V)sc->alpha : V(0);
+    const V al = MODE == 1 || MODE == 3 ? (V)sc->alpha : V(0);
     double rr = 0.0, rs = 0.0;
     if (tid == 0) {
         mbar_init(&bar);
@@ -227,28 +292,41 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
         band_load_tile(P, t, T);
         __syncthreads();
         const int64_t o0 = P.lev[0].off;
+        // level k0 comes from A (copied) or from r
+        const bool copy0 = MODE == 0 || (MODE == 3 && !P.first);
         if (T.rec.cbytes >= 0) {
             // thread 0 lays the tile out and starts the copies while the
-            // block takes level 0 from r (MODE 1, 2) into the region after
-            // the coefficients
+            // block takes level 0 from r (MODE 1, 2, 3 first band) into the
+            // region after the coefficients
             if (tid == 0) {
                 band_coef_offsets<V>(L, T);
                 // coefficients at 0, level-0 values after them (with the
                 // source's 16-byte phase when copied), levels 1..L after that
                 const int u0 = T.rec.cbytes;
                 const Span s0 = span(A, o0 + T.st[0], T.cnt[0], sizeof(V));
-                T.vs[0] = u0 + (MODE == 0 ? s0.head : 0);
+                T.vs[0] = u0 + (copy0 ? s0.head : 0);
                 int v = u0 + r16(16 + T.cnt[0] * (int)sizeof(V));
                 for (int j = 1; j <= L; ++j) {
                     T.vs[j] = v;
                     v += T.cnt[j] * (int)sizeof(V);
                 }
                 fence_async_smem();
-                mbar_expect(&bar, T.rec.cbytes + (MODE == 0 ? s0.bytes : 0));
+                mbar_expect(&bar, T.rec.cbytes + (copy0 ? s0.bytes : 0));
                 bulk_load(band_raw, P.coef + T.rec.cb, T.rec.cbytes, &bar);
-                if (MODE == 0) bulk_load(band_raw + u0, s0.src, s0.bytes, &bar);
+                if (copy0) bulk_load(band_raw + u0, s0.src, s0.bytes, &bar);
             }
-            if (MODE != 0) {
+            if (MODE == 3) {
+                // the CG step on levels 1..L, staged where the elimination
+                // adds them (the layout above must be visible first)
+                __syncthreads();
+                for (int j = 1; j <= L; ++j)
+                    band_cg_step(band_level_base(P, T, j), T.cnt[j], al, x, r, p, q,
+                                 reinterpret_cast<V *>(band_raw + T.vs[j]), rr, rs);
+            }
+            if (MODE == 3 && !copy0)
+                band_cg_step(o0 + T.st[0], T.cnt[0], al, x, r, p, q, reinterpret_cast<V *>(band_raw + T.rec.cbytes),
+                             rr, rs);
+            if (MODE != 3 && !copy0) {
                 // level 0 from r (after the CG step), four elements per thread in flight
                 V *v0 = reinterpret_cast<V *>(band_raw + T.rec.cbytes);
                 for (int i0 = tid; i0 < T.cnt[0]; i0 += 4 * kBandThreads) {
@@ -259,7 +337,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
                         if (i < T.cnt[0]) {
                             const int64_t u = T.st[0] + i;
                             rv[k] = r[u];
-                            if (MODE == 1) {
+                            if (MODE == 1 || MODE == 3) {
                                 xv[k] = x[u];
                                 pv[k] = p[u];
                                 qv[k] = q[u];
@@ -274,7 +352,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
                         if (i < T.cnt[0]) {
                             const int64_t u = T.st[0] + i;
                             V v = rv[k];
-                            if (MODE == 1) {
+                            if (MODE == 1 || MODE == 3) {
                                 x[u] = xv[k] + al * pv[k];
                                 v = v - al * qv[k];
                                 r[u] = v;
@@ -296,7 +374,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
             __syncthreads();
             const int jw = T.jw;
             for (int j = 0; j < jw; ++j) {
-                band_up_level(P, T, band_raw, j, F, 0, kBandThreads);
+                band_up_level<V, MODE == 3>(P, T, band_raw, j, F, 0, kBandThreads);
                 __syncthreads();
             }
             // the small top levels by warp 0 while the other warps store the
@@ -304,7 +382,7 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
             V *ds = P.scratch + T.rec.ds / (long long)sizeof(V);
             if (tid < 32) {
                 for (int j = jw; j < L; ++j) {
-                    band_up_level(P, T, band_raw, j, F, 0, 32);
+                    band_up_level<V, MODE == 3>(P, T, band_raw, j, F, 0, 32);
                     __syncwarp();
                 }
             } else {
@@ -331,7 +409,12 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
         } else {
             // oversized subtree: the same steps in place in global memory
             V *b0 = A + o0 + T.st[0];
-            for (int i = tid; i < T.cnt[0]; i += kBandThreads) {
+            if (MODE == 3)
+                for (int j = P.first ? 0 : 1; j <= L; ++j) {
+                    const int64_t g0 = band_level_base(P, T, j);
+                    band_cg_step(g0, T.cnt[j], al, x, r, p, q, A + g0, rr, rs);
+                }
+            for (int i = tid; MODE != 3 && i < T.cnt[0]; i += kBandThreads) {
                 const int64_t u = T.st[0] + i;
                 V v;
                 if (MODE == 1) {
@@ -355,8 +438,8 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
                 const int64_t onext = j + 1 < L ? P.lev[j + 1].off : P.off_top;
                 const int J0 = T.st[j + 1];
                 elim_level(A + Lv.off + T.st[j], A + onext + J0, Lv.seg + J0, T.st[j], Lv.inv + 4 * (int64_t)J0,
-                           Lv.lcf + 3 * ((int64_t)T.st[j] - 2 * (int64_t)J0), Lv.gamma, F, onext + J0,
-                           T.cnt[j + 1], 0, kBandThreads);
+                           Lv.lcf + 3 * ((int64_t)T.st[j] - 2 * (int64_t)J0), Lv.gamma,
+                           MODE == 3 ? static_cast<const V *>(A) : F, onext + J0, T.cnt[j + 1], 0, kBandThreads);
                 __syncthreads();
             }
         }
@@ -368,8 +451,9 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
     double v[2] = {rr, rs};
     block_sum<2>(v);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = v[0];
-        part[2 * blockIdx.x + 1] = v[1];
+        const int o = (MODE == 3 ? P.red_up : 0) + 2 * blockIdx.x;
+        part[o] = v[0];
+        part[o + 1] = v[1];
     }
     (void)ticket;
 }
@@ -385,6 +469,34 @@ __device__ __forceinline__ void band_down_level(const BandParams<V> &P, const Ba
                   0, P.pc, P.lev[j].dcoef, T.cnt[j + 1], tid0, nthr);
 }
 
+// sum z and r.z over `cnt` consecutive values z (shared or global) whose
+// expanded indices start at g0 (groups of four in V, then FP64).
+template <typename V>
+__device__ __forceinline__ void band_zred(const V *z, int64_t g0, int cnt, const V *__restrict__ r, double &sz,
+                                          double &srz)
+{
+    for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * kBandThreads) {
+        V rv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * kBandThreads;
+            if (i < cnt) rv[k] = r[g0 + i];
+        }
+        V a1 = V(0), a2 = V(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * kBandThreads;
+            if (i < cnt) {
+                const V zv = z[i];
+                a1 += zv;
+                a2 += rv[k] * zv;
+            }
+        }
+        sz += (double)a1;
+        srz += (double)a2;
+    }
+}
+
 // Downward band: for j = k1-1 .. k0, out_j(u) = pc * out_{j+1}(J) + dcoef_j *
 // D_j(u), starting from the level-k1 values in Yp.  The deltas come from the
 // band's scratch (DEXP false, written by the upward band) or from the
@@ -393,7 +505,11 @@ __device__ __forceinline__ void band_down_level(const BandParams<V> &P, const Ba
 // (expanded).  FINEST: out0 is the preconditioned residual z of the n-space
 // CG; reduces sum z, r.z, z.q and finalises zmean, rho, beta.  A tile in
 // global memory reads its deltas in place from D (A for the sweeps).
-template <typename V, bool FINEST, bool DEXP>
+// XRED (expanded-space CG, write_all, out0 = Y + offset of level k0): sums
+// z and r.z over every level of the band with r the expanded residual; the
+// first band finishes them with the tail's and the upper bands' partials
+// (n = ntilde) and sets the next direction's coefficients.
+template <typename V, bool FINEST, bool DEXP, bool XRED = false>
 __global__ void __launch_bounds__(kBandThreads, 2)
 k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V *out0, int write_all,
             int n, const V *__restrict__ r, const V *__restrict__ q, CgScalars *sc, double *part,
@@ -521,6 +637,10 @@ k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V
                     V *dst = Y + P.lev[j].off + T.st[j];
                     for (int i = tid; i < T.cnt[j]; i += kBandThreads) dst[i] = src[i];
                 }
+            if (XRED)
+                for (int j = 0; j < L; ++j)
+                    band_zred(reinterpret_cast<const V *>(band_raw + T.vs[j]), P.lev[j].off + T.st[j], T.cnt[j], r,
+                              sz, srz);
         } else {
             for (int j = L - 1; j >= 0; --j) {
                 const BandLevel<V> &Lv = P.lev[j];
@@ -539,8 +659,36 @@ k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V
                     srz += (double)r[u] * (double)zv;
                     if (flex) szq += (double)zv * (double)q[u];
                 }
+            if (XRED) {
+                __syncthreads();
+                for (int j = 0; j < L; ++j) {
+                    const int64_t g0 = P.lev[j].off + T.st[j];
+                    band_zred<V>(Y + g0, g0, T.cnt[j], r, sz, srz);
+                }
+            }
         }
         __syncthreads();
+    }
+    if (XRED) {
+        double v[2] = {sz, srz};
+        if (!P.first) {
+            block_sum<2>(v);
+            if (threadIdx.x == 0) {
+                part[P.red_dn + 2 * blockIdx.x] = v[0];
+                part[P.red_dn + 2 * blockIdx.x + 1] = v[1];
+            }
+            return;
+        }
+        if (grid_sum<2>(v, part + P.red_gs, ticket) && threadIdx.x == 0) {
+            // then the tail's pair and the upper bands' blocks, in order
+            for (int k = 0; k < P.xred_n; ++k) {
+                v[0] += __ldcg(part + P.xred_base + 2 * k);
+                v[1] += __ldcg(part + P.xred_base + 2 * k + 1);
+            }
+            const double m = v[0] / (double)n;
+            set_direction(sc, m, v[1] - m * sc->rs, 0.0);
+        }
+        return;
     }
     if (!FINEST) return;
     double v[3] = {sz, srz, szq};

@@ -66,6 +66,7 @@ template <typename V> struct DevCsr {
     int kernel = 0;
     int vec = 1;                       // SELL lane-group width (1, 2, 4)
     int sell_grid = 0;                 // SELL blocks per launch (0: one per 8 slices, capped)
+    int stream_hint = 0;               // 1: SELL and chunk entries loaded evict-first
 };
 
 template <typename V> struct DevMspLevel {
@@ -96,6 +97,11 @@ template <typename V> struct DevMsp {
     std::vector<BandParams<V>> band_n; // n-space MSP: gamma_k, dcoef c_k, pc 1
     std::vector<BandParams<V>> band_t; // expanded-space solve: gamma 1, dcoef 1, pc 1
     std::vector<BandParams<V>> band_p; // P(mu) by Horner: dcoef 1, pc -mu
+    // the expanded-space CG step and its reductions fused into band_t and
+    // tail_t (needs bands, a tail and room for the partials): up pairs of
+    // all bands, then the tail's down pair at xfuse_slot
+    bool xfuse = false;
+    int xfuse_fin_n = 0, xfuse_slot = 0;
 };
 
 // Reduction scratch + device scalars of one CG.

@@ -271,9 +271,11 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
         const std::vector<int> tops = plan_band_tops(m, t0, cap, sv);
         // resident band blocks: the grid, and the unit the tile count is balanced to
         for (const void *f : {(const void *)k_band_up<V, 0>, (const void *)k_band_up<V, 1>,
-                              (const void *)k_band_up<V, 2>, (const void *)k_band_down<V, true, false>,
+                              (const void *)k_band_up<V, 2>, (const void *)k_band_up<V, 3>,
+                              (const void *)k_band_down<V, true, false>,
                               (const void *)k_band_down<V, false, false>, (const void *)k_band_down<V, true, true>,
-                              (const void *)k_band_down<V, false, true>})
+                              (const void *)k_band_down<V, false, true>,
+                              (const void *)k_band_down<V, false, false, true>})
             LAP_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes));
         int occ_up = 0, occ_dn = 0;
         LAP_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_up, k_band_up<V, 1>, kBandThreads, kBandSmemBytes));
@@ -401,6 +403,29 @@ lap_status upload_msp(lap_handle_s &h, const HostModel &m, DevMsp<V> &d, const D
             d.band_p.push_back(P);
             k0 = k1;
         }
+        // partial pairs of the expanded-space CG fused into the sweep: the
+        // up pairs of every band, the tail's down pair, the upper bands'
+        // down pairs, then the first band's own grid reduction
+        if (!d.band_t.empty()) {
+            int off = 0;
+            for (size_t b = 0; b < d.band_t.size(); ++b) {
+                d.band_t[b].first = b == 0;
+                d.band_t[b].red_up = off;
+                off += 2 * d.band_t[b].grid_up;
+            }
+            d.xfuse_fin_n = off / 2;
+            d.xfuse_slot = off;
+            off += 2;
+            for (size_t b = 1; b < d.band_t.size(); ++b) {
+                d.band_t[b].red_dn = off;
+                off += 2 * d.band_t[b].grid_down;
+            }
+            d.band_t[0].xred_base = d.xfuse_slot;
+            d.band_t[0].xred_n = (off - d.xfuse_slot) / 2;
+            d.band_t[0].red_gs = off;
+            off += 2 * d.band_t[0].grid_down;
+            d.xfuse = off <= kMaxRedBlocks * kRedSlots;
+        }
     }
     return LAP_OK;
 }
@@ -452,22 +477,23 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
 template <typename V>
 void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
 {
-    struct Cand { int kernel, grid; };
+    struct Cand { int kernel, grid, hint; };
     std::vector<Cand> cand;
     const int64_t need = (static_cast<int64_t>(A.nslices + A.nlong) * 32 + kBlock - 1) / kBlock;
     for (int waves = 1; waves <= 3; ++waves) {
         const int64_t g = std::min<int64_t>(need, int64_t(h.grid_cap) * waves);
         if (g > kMaxRedBlocks * kRedSlots / 2) break;
         if (waves > 1 && g <= int64_t(h.grid_cap) * (waves - 1)) break;   // no new launch shape
-        cand.push_back({-1, static_cast<int>(std::max<int64_t>(g, 1))});
+        for (int hint = 0; hint < 2; ++hint) cand.push_back({-1, static_cast<int>(std::max<int64_t>(g, 1)), hint});
     }
-    for (int t : {2, 4, 8, 16}) cand.push_back({t, 0});
+    for (int t : {2, 4, 8, 16}) cand.push_back({t, 0, 0});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return;
     Cand best = cand[0];
     float best_ms = 1e30f;
     for (const Cand &c : cand) {
         A.sell_grid = c.grid;
+        A.stream_hint = c.hint;
         spmv<V, 2>(h, A, c.kernel, x, y, nullptr, nullptr, h.stb, h.s);
         cudaEventRecord(e0, h.s);
         for (int i = 0; i < 5; ++i) spmv<V, 2>(h, A, c.kernel, x, y, nullptr, nullptr, h.stb, h.s);
@@ -485,6 +511,7 @@ void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
     (void)cudaGetLastError();
     A.kernel = best.kernel < 0 ? 0 : best.kernel;
     A.sell_grid = best.grid;
+    A.stream_hint = best.hint;
 }
 
 // --------------------------------------------------------------------------
@@ -496,22 +523,34 @@ void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, 
 {
     if (tpr == 0) tpr = A.kernel;      // 0: the tuned choice, -1: SELL, t > 0: CSR
     if (tpr <= 0) {
+        const bool hint = A.stream_hint != 0;
         if (A.nchunks > 0) {
             h.launches += 1;
-            k_long_chunks<V><<<grid_for(h, static_cast<int64_t>(A.nchunks) * 32), kBlock, 0, s>>>(
-                A.nchunks, A.chunk_row, A.chunk_beg, A.lrow, A.lci, A.lw, x, A.chunk_part, st.sc,
-                MODE != 2);
+            const int gc = grid_for(h, static_cast<int64_t>(A.nchunks) * 32);
+            if (hint)
+                k_long_chunks<V, true><<<gc, kBlock, 0, s>>>(A.nchunks, A.chunk_row, A.chunk_beg, A.lrow, A.lci,
+                                                             A.lw, x, A.chunk_part, st.sc, MODE != 2);
+            else
+                k_long_chunks<V, false><<<gc, kBlock, 0, s>>>(A.nchunks, A.chunk_row, A.chunk_beg, A.lrow, A.lci,
+                                                              A.lw, x, A.chunk_part, st.sc, MODE != 2);
         }
         h.launches += 1;
         const int g = A.sell_grid > 0 ? A.sell_grid
                                       : grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
-#define LAP_SELL(VEC)                                                                                   \
-    k_sell<V, MODE, VEC><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.rowperm, A.eci, A.ew, A.nlong, A.lrow, \
-                                              A.lchunk_ptr, A.chunk_part, x, y, bs, yres, st.sc, st.part,   \
-                                              st.ticket)
-        if (A.vec == 4) LAP_SELL(4);
-        else if (A.vec == 2) LAP_SELL(2);
-        else LAP_SELL(1);
+#define LAP_SELL(VEC, HINT)                                                                                      \
+    k_sell<V, MODE, VEC, HINT><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.rowperm, A.eci, A.ew,      \
+                                                    A.nlong, A.lrow, A.lchunk_ptr, A.chunk_part, x, y, bs, yres, \
+                                                    st.sc, st.part, st.ticket)
+        if (A.vec == 4) {
+            if (hint) LAP_SELL(4, true);
+            else LAP_SELL(4, false);
+        } else if (A.vec == 2) {
+            if (hint) LAP_SELL(2, true);
+            else LAP_SELL(2, false);
+        } else {
+            if (hint) LAP_SELL(1, true);
+            else LAP_SELL(1, false);
+        }
 #undef LAP_SELL
         return;
     }
@@ -778,12 +817,48 @@ void prolong_tilde_to_z(const lap_handle_s &h, const DevMsp<V> &M, const V *yt, 
 
 // One expanded-space CG iteration of the PEGP inner solve L_H y~ = r~ with the
 // MSP preconditioner (vectors e: x = y~, r = r~, p, q, z unused, A/Y sweeps).
+// With the bands and the tail in place the step x += alpha p, r -= alpha q
+// and the reductions of z = M r run inside the sweep (q = L_H p, bands up
+// with the step, tail with the convergence test, bands down with sum z and
+// r.z, p = Pi z + beta p); otherwise step, sweep and reductions are
+// separate launches.
 template <typename V>
 void inner_iteration(const lap_handle_s &h, const DevCsr<V> &H, const DevMsp<V> &M,
                      const CgVectors<V> &e, const CgState &st, cudaStream_t s)
 {
     const int64_t nt = M.off[M.levels];
     spmv<V, 0>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
+    if (M.xfuse) {
+        const size_t nb = M.band_t.size();
+        h.launches += static_cast<int64_t>(2 * nb + 1);
+        for (size_t b = 0; b < nb; ++b) {
+            const BandParams<V> &P = M.band_t[b];
+            k_band_up<V, 3><<<P.grid_up, kBandThreads, static_cast<size_t>(P.smem), s>>>(
+                P, e.x, e.r, e.p, e.q, e.A, nullptr, st.sc, st.part, st.ticket);
+        }
+        TailParams<V> T = M.tail_t;
+        T.A = e.A;
+        T.Y = e.Y;
+        T.F = e.r;
+        T.fin = 3;
+        T.fin_n = M.xfuse_fin_n;
+        T.fin_part = st.part;
+        T.cx = e.x;
+        T.cr = e.r;
+        T.cp = e.p;
+        T.cq = e.q;
+        T.xred_slot = M.xfuse_slot;
+        T.xred_part = st.part;
+        k_msp_tail<V><<<1, 1024, M.tail_smem, s>>>(T, st.sc);
+        for (size_t b = nb; b-- > 0;) {
+            const BandParams<V> &P = M.band_t[b];
+            k_band_down<V, false, false, true><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
+                P, e.A, e.Y, e.Y, e.Y + P.lev[0].off, 1, static_cast<int>(nt), e.r, nullptr, st.sc, st.part,
+                st.ticket);
+        }
+        pupdate<V>(h, nt, e.Y, e.p, st, s);
+        return;
+    }
     h.launches += 2;
     k_update<V, true, false><<<grid_for(h, nt), kBlock, 0, s>>>(static_cast<int>(nt), e.x, e.r, e.p,
                                                                 e.q, e.A, st.sc, st.part, st.ticket);
@@ -1748,12 +1823,44 @@ double band_up_bytes(const DevMsp<V> &M)
 }
 }  // namespace
 
+// Algorithmic bytes of the expanded-space MSP solve y~ = L_T^+ f: f read,
+// every level's segments and elimination coefficients read once, the deltas
+// of every level below the top stored on the way up and read on the way down,
+// y~ written, the top pseudo-inverse read.
+template <typename V>
+double sweep_tilde_bytes(const DevMsp<V> &M)
+{
+    const double s = sizeof(V);
+    const int l = M.levels;
+    const double nt = static_cast<double>(M.off[l]);
+    double b = 2.0 * s * nt + 2.0 * s * (nt - M.ntop) + 8.0 * M.ntop * M.ntop;
+    for (int k = 0; k + 1 < l; ++k) {
+        const double na = M.lev[k].nagg, nl = M.lev[k].n - 2 * na;
+        b += 4.0 * (na + 1) + s * (4 * na + 3 * nl);
+    }
+    return b;
+}
+
+// One inner CG iteration: the L_H matvec (entries, row pointers, p read once,
+// q written), the step (x, p, q, r read; x, r written), the sweep without its
+// right-hand side read (the updated r is used where it is produced), r read
+// again for r.z, and p = Pi z + beta p (z, p read, p written).
+template <typename V>
+double inner_iteration_bytes(const DevCsr<V> &H, const DevMsp<V> &M)
+{
+    const double s = sizeof(V);
+    const double nt = static_cast<double>(M.off[M.levels]);
+    const double mv = H.nnz * (4.0 + s) + 4.0 * (H.n + 1) + 2.0 * s * H.n;
+    return mv + 6.0 * s * nt + (sweep_tilde_bytes(M) - s * nt) + s * nt + 3.0 * s * nt;
+}
+
 lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, double *ms, double *bytes)
 {
     if (precision == 1 && !h.L32.w) return LAP_ERR_INVALID_ARG;
-    if (kernel == 1 && !h.H64.w) return LAP_ERR_INVALID_ARG;
+    if ((kernel == 1 || kernel == 7 || kernel == 8) && !h.H64.w) return LAP_ERR_INVALID_ARG;
+    if ((kernel == 7 || kernel == 8) && (h.M64.levels < 2 || !is_pegp(h))) return LAP_ERR_INVALID_ARG;
     if (kernel == 6 && !h.G64) return LAP_ERR_INVALID_ARG;
-    if (kernel < 0 || kernel > 6) return LAP_ERR_INVALID_ARG;
+    if (kernel < 0 || kernel > 8) return LAP_ERR_INVALID_ARG;
     const cudaStream_t s = h.s;
     cudaEvent_t e0, e1;
     LAP_CK(cudaEventCreate(&e0));
@@ -1791,6 +1898,8 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
                     static_cast<int>(nt), h.g_ld, Sel<V>::G(h), Sel<V>::e(h).r, Sel<V>::e(h).x, h.stb.sc);
                 break;
             }
+            case 7: inner_iteration<V>(h, Sel<V>::H(h), M, Sel<V>::e(h), h.stb, s); break;
+            case 8: msp_tilde<V>(h, M, Sel<V>::e(h).A, Sel<V>::e(h).Y, h.stb.sc, s); break;
             default: {
                 const BandParams<V> &P = M.band_n[0];
                 k_band_down<V, true, false><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
@@ -1822,6 +1931,19 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
             // exact PEGP matvec: G (ntilde^2) and r~ read, y~ written
             const double nt = static_cast<double>(M.off[M.levels]);
             by = sv * nt * nt + 2.0 * sv * nt;
+        } else if (kernel == 7) {
+            by = inner_iteration_bytes(Sel<V>::H(h), M);
+            // a direction, a residual and an iterate to start from
+            const auto &e = Sel<V>::e(h);
+            const int64_t nt = M.off[M.levels];
+            k_bench_fill<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.p, 0x1234567u);
+            k_bench_fill<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.r, 0x7654321u);
+            k_bench_fill<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.x, 0x0badf00du);
+        } else if (kernel == 8) {
+            by = sweep_tilde_bytes(M);
+            const auto &e = Sel<V>::e(h);
+            const int64_t nt = M.off[M.levels];
+            k_bench_fill<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.A, 0x2468aceu);
         } else {
             if (M.band_n.empty()) return -1.0;
             // first band down: deltas and segments of its levels read, the
@@ -1831,6 +1953,8 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
             for (int k = 0; k < P.nlev; ++k) by += sv * M.lev[k].n + 4.0 * (M.lev[k].nagg + 1);
             by += sv * static_cast<double>(M.off[P.nlev + 1] - M.off[P.nlev]);
         }
+        // (kernel 8 overwrites its right-hand side in A with deltas; the values
+        // it leaves are as valid a right-hand side for the next launch)
         launch();                                   // warm-up
         cudaEventRecord(e0, s);
         for (int i = 0; i < reps; ++i) launch();
@@ -1850,6 +1974,12 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
     cudaEventDestroy(e1);
     *ms = static_cast<double>(t) / reps;
     *bytes = by;
+    if (kernel == 7) {
+        // every timed iteration must have run to its end
+        CgScalars sc;
+        LAP_TRY(poll(h, h.stb, sc));
+        if (sc.flag != kRun) return LAP_ERR_BREAKDOWN;
+    }
     return LAP_OK;
 }
 

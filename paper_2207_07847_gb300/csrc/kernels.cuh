@@ -247,54 +247,63 @@ __device__ __forceinline__ void spmv_finish(int row, V xi, V s, V *y, const doub
     }
 }
 
+// Loads of a matrix entry stream: HINT marks them evict-first (each entry is
+// read once per product), so that the gathered vector stays in L2.
+template <bool HINT, typename T>
+__device__ __forceinline__ T ldm(const T *p)
+{
+    if (HINT) return __ldcs(p);
+    return __ldg(p);
+}
+
 // VEC consecutive entries of one lane (a lane group of the SELL layout) with
 // vector loads; the row sum is still accumulated entry by entry.
-template <typename V, int VEC> struct LaneGroup;
-template <typename V> struct LaneGroup<V, 1> {
+template <typename V, int VEC, bool HINT = false> struct LaneGroup;
+template <typename V, bool HINT> struct LaneGroup<V, 1, HINT> {
     __device__ __forceinline__ static V add(V s, V xi, const int *c, const V *w, const V *__restrict__ x)
     {
-        return s + w[0] * (xi - x[c[0]]);
+        return s + ldm<HINT>(w) * (xi - x[ldm<HINT>(c)]);
     }
 };
-template <> struct LaneGroup<float, 2> {
+template <bool HINT> struct LaneGroup<float, 2, HINT> {
     __device__ __forceinline__ static float add(float s, float xi, const int *c, const float *w,
                                                 const float *__restrict__ x)
     {
-        const int2 cc = __ldg(reinterpret_cast<const int2 *>(c));
-        const float2 ww = __ldg(reinterpret_cast<const float2 *>(w));
+        const int2 cc = ldm<HINT>(reinterpret_cast<const int2 *>(c));
+        const float2 ww = ldm<HINT>(reinterpret_cast<const float2 *>(w));
         s += ww.x * (xi - x[cc.x]);
         return s + ww.y * (xi - x[cc.y]);
     }
 };
-template <> struct LaneGroup<float, 4> {
+template <bool HINT> struct LaneGroup<float, 4, HINT> {
     __device__ __forceinline__ static float add(float s, float xi, const int *c, const float *w,
                                                 const float *__restrict__ x)
     {
-        const int4 cc = __ldg(reinterpret_cast<const int4 *>(c));
-        const float4 ww = __ldg(reinterpret_cast<const float4 *>(w));
+        const int4 cc = ldm<HINT>(reinterpret_cast<const int4 *>(c));
+        const float4 ww = ldm<HINT>(reinterpret_cast<const float4 *>(w));
         s += ww.x * (xi - x[cc.x]);
         s += ww.y * (xi - x[cc.y]);
         s += ww.z * (xi - x[cc.z]);
         return s + ww.w * (xi - x[cc.w]);
     }
 };
-template <> struct LaneGroup<double, 2> {
+template <bool HINT> struct LaneGroup<double, 2, HINT> {
     __device__ __forceinline__ static double add(double s, double xi, const int *c, const double *w,
                                                  const double *__restrict__ x)
     {
-        const int2 cc = __ldg(reinterpret_cast<const int2 *>(c));
-        const double2 ww = __ldg(reinterpret_cast<const double2 *>(w));
+        const int2 cc = ldm<HINT>(reinterpret_cast<const int2 *>(c));
+        const double2 ww = ldm<HINT>(reinterpret_cast<const double2 *>(w));
         s += ww.x * (xi - x[cc.x]);
         return s + ww.y * (xi - x[cc.y]);
     }
 };
-template <> struct LaneGroup<double, 4> {
+template <bool HINT> struct LaneGroup<double, 4, HINT> {
     __device__ __forceinline__ static double add(double s, double xi, const int *c, const double *w,
                                                  const double *__restrict__ x)
     {
-        const int4 cc = __ldg(reinterpret_cast<const int4 *>(c));
-        const double2 w0 = __ldg(reinterpret_cast<const double2 *>(w));
-        const double2 w1 = __ldg(reinterpret_cast<const double2 *>(w) + 1);
+        const int4 cc = ldm<HINT>(reinterpret_cast<const int4 *>(c));
+        const double2 w0 = ldm<HINT>(reinterpret_cast<const double2 *>(w));
+        const double2 w1 = ldm<HINT>(reinterpret_cast<const double2 *>(w) + 1);
         s += w0.x * (xi - x[cc.x]);
         s += w0.y * (xi - x[cc.y]);
         s += w1.x * (xi - x[cc.z]);
@@ -303,7 +312,7 @@ template <> struct LaneGroup<double, 4> {
 };
 
 // Partial sums of the long rows, one warp per chunk of <= 4096 entries.
-template <typename V>
+template <typename V, bool HINT = false>
 __global__ void __launch_bounds__(kBlock)
 k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__restrict__ chunk_beg,
               const int *__restrict__ lrow, const int *__restrict__ lci, const V *__restrict__ lw,
@@ -319,7 +328,7 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
         // lane l takes entries 128 g + 4 l .. + 3 with one vector load each
 #pragma unroll 2
         for (int64_t p = chunk_beg[c] + 4 * lane; p < chunk_beg[c + 1]; p += 128)
-            s = LaneGroup<V, 4>::add(s, xi, lci + p, lw + p, x);
+            s = LaneGroup<V, 4, HINT>::add(s, xi, lci + p, lw + p, x);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) chunk_part[c] = s;
@@ -331,7 +340,7 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
 // time (see make_sell for the layout); long rows add their chunk partials.
 // The warps stride over the slices; the grid (one or more waves of resident
 // blocks) is chosen per matrix at setup by timing.
-template <typename V, int MODE, int VEC>
+template <typename V, int MODE, int VEC, bool HINT = false>
 __global__ void __launch_bounds__(kBlock)
 k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__restrict__ lmask,
        const int *__restrict__ rowperm, const int *__restrict__ eci, const V *__restrict__ ew, int nlong,
@@ -357,7 +366,8 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
         const V *pw = ew + base + lane * VEC;
         const int ng = width / VEC;
 #pragma unroll(VEC == 1 ? 4 : 2)
-        for (int g = 0; g < ng; ++g) s = LaneGroup<V, VEC>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
+        for (int g = 0; g < ng; ++g)
+            s = LaneGroup<V, VEC, HINT>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
         if (valid && !((lmask[task] >> lane) & 1u)) spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
     };
     auto long_row = [&](int li) {
@@ -767,9 +777,18 @@ template <typename V> struct TailParams {
     int write_all;            // write every tail level of Y (else the first only)
     // finishing the first band's reductions: 0 none, 1 after the CG step
     // (iteration count, relative residual, convergence test), 2 without it;
-    // fin_n per-block pairs (||r||^2, sum r) in fin_part
+    // fin_n per-block pairs (||r||^2, sum r) in fin_part.  3: the expanded-
+    // space CG fused into the sweep: the step x += alpha p, r -= alpha q on
+    // the tail's levels above its first (expanded vectors cx, cr, cp, cq; F
+    // is cr), then as 1 over every band's pairs and the tail's own terms
     int fin, fin_n;
     const double *fin_part;
+    V *cx = nullptr, *cr = nullptr;
+    const V *cp = nullptr, *cq = nullptr;
+    // >= 0 (with fin 3): sum z and r.z over the tail's levels to
+    // xred_part[xred_slot], xred_part[xred_slot + 1]
+    int xred_slot = -1;
+    double *xred_part = nullptr;
     TailLevel<V> lev[kTailMaxLevels];
 };
 
@@ -788,11 +807,24 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
             v[0] += P.fin_part[2 * b];
             v[1] += P.fin_part[2 * b + 1];
         }
+        if (P.fin == 3) {
+            // the CG step on the levels above the tail's first
+            const V al = (V)sc->alpha;
+            const int nup = P.ntail - P.n0;
+            for (int i = threadIdx.x; i < nup; i += blockDim.x) {
+                const int64_t u = P.off0 + P.n0 + i;
+                P.cx[u] += al * P.cp[u];
+                const V rv = P.cr[u] - al * P.cq[u];
+                P.cr[u] = rv;
+                v[0] += (double)rv * (double)rv;
+                v[1] += (double)rv;
+            }
+        }
         block_sum<2>(v);
         if (threadIdx.x == 0) {
             sc->rr = v[0];
             sc->rs = v[1];
-            if (P.fin == 1) {
+            if (P.fin == 1 || P.fin == 3) {
                 finish_step(sc, v[0]);
             }
             stop = sc->flag != kRun;
@@ -875,6 +907,20 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
     }
     const int nout = P.write_all ? P.ntail : P.n0;
     for (int i = tid; i < nout; i += nth) P.Y[P.off0 + i] = sz[i];
+    if (P.xred_slot >= 0) {
+        // sum z and r.z over the tail's levels for the expanded-space CG
+        double v[2] = {0.0, 0.0};
+        for (int i = tid; i < P.ntail; i += nth) {
+            const double zv = (double)sz[i];
+            v[0] += zv;
+            v[1] += (double)P.cr[P.off0 + i] * zv;
+        }
+        block_sum<2>(v);
+        if (tid == 0) {
+            P.xred_part[P.xred_slot] = v[0];
+            P.xred_part[P.xred_slot + 1] = v[1];
+        }
+    }
 }
 
 // Restriction of one level: s_{k+1}(J) = sum_{u in J} s_k(u); the scaled value
@@ -1102,6 +1148,20 @@ static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flex
 }
 
 // scalars for timing runs: running, never converging, unit norms
+// Fixed values in [-1, 1) for timing runs (a hash of the index; not random
+// numbers of the method).
+template <typename V>
+__global__ void k_bench_fill(int64_t n, V *v, uint32_t salt)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = static_cast<uint32_t>(i) * 2654435761u ^ salt;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        v[i] = static_cast<V>(static_cast<double>(h) * (2.0 / 4294967296.0) - 1.0);
+    }
+}
+
 static __global__ void k_bench_scalars(CgScalars *sc)
 {
     sc->tol = -1.0;                 // never met, even by a zero residual

@@ -109,9 +109,6 @@ ITER_SPREAD = {
     ("batched_grid3d_18", "none", 0): 14,
     ("batched_grid3d_18", "none", 5): 3,
     ("served_grid2d_56x40", "msp"): 7,
-    # total inner iterations of PEGP with inner tolerance 1e-6 (its inner
-    # stopping tests come within 2e-4 of flipping)
-    ("grid2d_64", "pegp_inner_tol1e-6", "inner_total"): 171,
 }
 
 

@@ -89,14 +89,11 @@ def _variant(v, g, kind, b, mu, seed, coarse_max, krylov, restart, inner_tol, in
 
 
 def _spread(g, kind, b, *, mu=0.8, seed=17, coarse_max=32, krylov="cg", restart=30,
-            inner_tol=1e-6, inner_maxit=500, with_inner=False):
+            inner_tol=1e-6, inner_maxit=500):
     args = (g, kind, b, mu, seed, coarse_max, krylov, restart, inner_tol, inner_maxit)
     futs = [_pool().submit(_variant, v, *args) for v in range(2 + PERTURBED_RUNS)]
     res = [f.result() for f in futs]
     counts = [c for c, _ in res]
-    inner = [i for _, i in res]
-    if with_inner:
-        return max(counts) - min(counts), counts, max(inner) - min(inner), inner
     return max(counts) - min(counts), counts
 
 
@@ -190,13 +187,12 @@ def test_spread_of_the_oracle_checked_batched_and_served_columns():
 
 
 def test_spread_of_the_pegp_inner_case():
-    """PEGP with an inner CG to 1e-6: the outer count is stable, the total of
-    inner iterations moves with the inner stopping tests that rounding flips."""
+    """PEGP with an inner CG to 1e-6: the outer count is stable (the total of
+    inner iterations moves with the inner stopping tests that rounding flips
+    and is not compared)."""
     g = PARITY_GRAPHS["grid2d_64"]()
-    spread, counts, ispread, inner = _spread(g, "pegp_inner", gg.rhs(g.n, seed=8),
-                                             inner_tol=1e-6, inner_maxit=500, with_inner=True)
+    spread, counts = _spread(g, "pegp_inner", gg.rhs(g.n, seed=8), inner_tol=1e-6, inner_maxit=500)
     _check(("grid2d_64", "pegp_inner_tol1e-6"), spread, counts)
-    _check(("grid2d_64", "pegp_inner_tol1e-6", "inner_total"), ispread, inner)
 
 
 @pytest.mark.parametrize("mu", [1 / 64, 0.3, 0.8])

@@ -316,16 +316,12 @@ k_band_up(const BandParams<V> P, V *__restrict__ x, V *r, const V *__restrict__ 
                 if (copy0) bulk_load(band_raw + u0, s0.src, s0.bytes, &bar);
             }
             if (MODE == 3) {
-                // the CG step on levels 1..L, staged where the elimination
-                // adds them (the layout above must be visible first)
+                // the CG step on levels 0 (first band) or 1 .. L, staged where
+                // the elimination adds them (the layout above must be visible
+                // first)
                 __syncthreads();
-                for (int j = 1; j <= L; ++j)
-                    band_cg_step(band_level_base(P, T, j), T.cnt[j], al, x, r, p, q,
-                                 reinterpret_cast<V *>(band_raw + T.vs[j]), rr, rs);
+                band_cg_levels(P, T, band_raw, copy0 ? 1 : 0, L, al, x, r, p, q, rr, rs);
             }
-            if (MODE == 3 && !copy0)
-                band_cg_step(o0 + T.st[0], T.cnt[0], al, x, r, p, q, reinterpret_cast<V *>(band_raw + T.rec.cbytes),
-                             rr, rs);
             if (MODE != 3 && !copy0) {
                 // level 0 from r (after the CG step), four elements per thread in flight
                 V *v0 = reinterpret_cast<V *>(band_raw + T.rec.cbytes);
@@ -467,6 +463,115 @@ __device__ __forceinline__ void band_down_level(const BandParams<V> &P, const Ba
     V *o = reinterpret_cast<V *>(sm + T.vs[j]);
     prolong_level(o, o, reinterpret_cast<const V *>(sm + T.vs[j + 1]), reinterpret_cast<const int *>(sm + T.ss[j]),
                   0, P.pc, P.lev[j].dcoef, T.cnt[j + 1], tid0, nthr);
+}
+
+// The elements of levels j0..j1 of a staged tile taken as one sequence:
+// element t lies on level lv at index ix.  `lv`, `base` carry the level of an
+// earlier element and the sequence index of that level's first element, so
+// a thread walking t upwards steps through the levels once.
+__device__ __forceinline__ void band_locate(const BandTile &T, int t, int &lv, int &base)
+{
+    while (t >= base + T.cnt[lv]) {
+        base += T.cnt[lv];
+        ++lv;
+    }
+}
+
+// CG step on every level j0..j1 of a staged tile, the updated r staged at
+// the level's values in shared memory: the levels taken as one sequence, so
+// that each thread keeps G elements in flight across level boundaries.
+template <typename V>
+__device__ __forceinline__ void band_cg_levels(const BandParams<V> &P, const BandTile &T, unsigned char *sm, int j0,
+                                               int j1, V al, V *__restrict__ x, V *__restrict__ r,
+                                               const V *__restrict__ p, const V *__restrict__ q, double &rr,
+                                               double &rs)
+{
+    constexpr int G = sizeof(V) == 4 ? 4 : 2;
+    int tot = 0;
+    for (int j = j0; j <= j1; ++j) tot += T.cnt[j];
+    int lv0 = j0, base0 = 0;
+    for (int t0 = threadIdx.x; t0 < tot; t0 += G * kBandThreads) {
+        int lv[G], ix[G];
+        V xv[G], pv[G], qv[G], rv[G];
+        int l = lv0, b = base0;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int t = t0 + k * kBandThreads;
+            lv[k] = -1;
+            if (t < tot) {
+                band_locate(T, t, l, b);
+                if (k == 0) {
+                    lv0 = l;
+                    base0 = b;
+                }
+                lv[k] = l;
+                ix[k] = t - b;
+                const int64_t u = band_level_base(P, T, l) + ix[k];
+                xv[k] = x[u];
+                pv[k] = p[u];
+                qv[k] = q[u];
+                rv[k] = r[u];
+            }
+        }
+        V r2 = V(0), r1 = V(0);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            if (lv[k] >= 0) {
+                const int64_t u = band_level_base(P, T, lv[k]) + ix[k];
+                x[u] = xv[k] + al * pv[k];
+                const V v = rv[k] - al * qv[k];
+                r[u] = v;
+                reinterpret_cast<V *>(sm + T.vs[lv[k]])[ix[k]] = v;
+                r2 += v * v;
+                r1 += v;
+            }
+        }
+        rr += (double)r2;
+        rs += (double)r1;
+    }
+}
+
+// sum z and r.z over levels 0..L-1 of a staged tile (z at the levels' values
+// in shared memory, r global), as one sequence with G loads in flight.
+template <typename V>
+__device__ __forceinline__ void band_zred_levels(const BandParams<V> &P, const BandTile &T, const unsigned char *sm,
+                                                 const V *__restrict__ r, double &sz, double &srz)
+{
+    constexpr int G = sizeof(V) == 4 ? 8 : 4;
+    int tot = 0;
+    for (int j = 0; j < P.nlev; ++j) tot += T.cnt[j];
+    int lv0 = 0, base0 = 0;
+    for (int t0 = threadIdx.x; t0 < tot; t0 += G * kBandThreads) {
+        int lv[G], ix[G];
+        V rv[G];
+        int l = lv0, b = base0;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int t = t0 + k * kBandThreads;
+            lv[k] = -1;
+            if (t < tot) {
+                band_locate(T, t, l, b);
+                if (k == 0) {
+                    lv0 = l;
+                    base0 = b;
+                }
+                lv[k] = l;
+                ix[k] = t - b;
+                rv[k] = r[P.lev[l].off + T.st[l] + ix[k]];
+            }
+        }
+        V a1 = V(0), a2 = V(0);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            if (lv[k] >= 0) {
+                const V zv = reinterpret_cast<const V *>(sm + T.vs[lv[k]])[ix[k]];
+                a1 += zv;
+                a2 += rv[k] * zv;
+            }
+        }
+        sz += (double)a1;
+        srz += (double)a2;
+    }
 }
 
 // sum z and r.z over `cnt` consecutive values z (shared or global) whose
@@ -637,10 +742,7 @@ k_band_down(const BandParams<V> P, const V *__restrict__ D, const V *Yp, V *Y, V
                     V *dst = Y + P.lev[j].off + T.st[j];
                     for (int i = tid; i < T.cnt[j]; i += kBandThreads) dst[i] = src[i];
                 }
-            if (XRED)
-                for (int j = 0; j < L; ++j)
-                    band_zred(reinterpret_cast<const V *>(band_raw + T.vs[j]), P.lev[j].off + T.st[j], T.cnt[j], r,
-                              sz, srz);
+            if (XRED) band_zred_levels(P, T, band_raw, r, sz, srz);
         } else {
             for (int j = L - 1; j >= 0; --j) {
                 const BandLevel<V> &Lv = P.lev[j];

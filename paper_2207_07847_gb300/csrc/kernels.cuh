@@ -354,6 +354,24 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     double a0 = 0.0, a1 = 0.0;
+    // MODE 0 in FP32: the products of up to four rows summed in V, then in FP64
+    V g0 = V(0), g1 = V(0);
+    int gc = 0;
+    auto finish = [&](int row, V xi, V s) {
+        if (MODE == 0 && sizeof(V) == 4) {
+            y[row] = s;
+            g0 += xi * s;
+            g1 += s;
+            if (++gc == 4) {
+                a0 += (double)g0;
+                a1 += (double)g1;
+                g0 = g1 = V(0);
+                gc = 0;
+            }
+        } else {
+            spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
+        }
+    };
     auto slice = [&](int task) {
         const int slot = task * 32 + lane;
         const int row = rowperm ? rowperm[slot] : (slot < n ? slot : -1);
@@ -368,14 +386,14 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
 #pragma unroll(VEC == 1 ? 4 : 2)
         for (int g = 0; g < ng; ++g)
             s = LaneGroup<V, VEC, HINT>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
-        if (valid && !((lmask[task] >> lane) & 1u)) spmv_finish<V, MODE>(row, xi, s, y, bs, yres, a0, a1);
+        if (valid && !((lmask[task] >> lane) & 1u)) finish(row, xi, s);
     };
     auto long_row = [&](int li) {
         // long row: add its chunk partials in chunk order
         const int row = lrow[li];
         V s = V(0);
         for (int c = lchunk_ptr[li]; c < lchunk_ptr[li + 1]; ++c) s += chunk_part[c];
-        spmv_finish<V, MODE>(row, x[row], s, y, bs, yres, a0, a1);
+        finish(row, x[row], s);
     };
     const int ntask = nslices + nlong;
     for (int task = gwarp; task < ntask; task += nwarp) {          // warp-uniform
@@ -383,6 +401,8 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
         else if (lane == 0) long_row(task - nslices);
     }
     if (MODE == 2) return;
+    a0 += (double)g0;
+    a1 += (double)g1;
     double v[2] = {a0, a1};
     if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
         if (MODE == 0) {
@@ -808,16 +828,34 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
             v[1] += P.fin_part[2 * b + 1];
         }
         if (P.fin == 3) {
-            // the CG step on the levels above the tail's first
+            // the CG step on the levels above the tail's first, four
+            // elements per thread in flight
             const V al = (V)sc->alpha;
             const int nup = P.ntail - P.n0;
-            for (int i = threadIdx.x; i < nup; i += blockDim.x) {
-                const int64_t u = P.off0 + P.n0 + i;
-                P.cx[u] += al * P.cp[u];
-                const V rv = P.cr[u] - al * P.cq[u];
-                P.cr[u] = rv;
-                v[0] += (double)rv * (double)rv;
-                v[1] += (double)rv;
+            const int64_t b0 = P.off0 + P.n0;
+            for (int i0 = threadIdx.x; i0 < nup; i0 += 4 * (int)blockDim.x) {
+                V xv[4], pv[4], qv[4], rv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * (int)blockDim.x;
+                    if (i < nup) {
+                        xv[k] = P.cx[b0 + i];
+                        pv[k] = P.cp[b0 + i];
+                        qv[k] = P.cq[b0 + i];
+                        rv[k] = P.cr[b0 + i];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * (int)blockDim.x;
+                    if (i < nup) {
+                        P.cx[b0 + i] = xv[k] + al * pv[k];
+                        const V r1 = rv[k] - al * qv[k];
+                        P.cr[b0 + i] = r1;
+                        v[0] += (double)r1 * (double)r1;
+                        v[1] += (double)r1;
+                    }
+                }
             }
         }
         block_sum<2>(v);
@@ -910,10 +948,22 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
     if (P.xred_slot >= 0) {
         // sum z and r.z over the tail's levels for the expanded-space CG
         double v[2] = {0.0, 0.0};
-        for (int i = tid; i < P.ntail; i += nth) {
-            const double zv = (double)sz[i];
-            v[0] += zv;
-            v[1] += (double)P.cr[P.off0 + i] * zv;
+        for (int i0 = tid; i0 < P.ntail; i0 += 8 * nth) {
+            V rv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * nth;
+                if (i < P.ntail) rv[k] = P.cr[P.off0 + i];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * nth;
+                if (i < P.ntail) {
+                    const double zv = (double)sz[i];
+                    v[0] += zv;
+                    v[1] += (double)rv[k] * zv;
+                }
+            }
         }
         block_sum<2>(v);
         if (tid == 0) {

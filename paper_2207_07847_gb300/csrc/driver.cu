@@ -827,8 +827,12 @@ void inner_iteration(const lap_handle_s &h, const DevCsr<V> &H, const DevMsp<V> 
                      const CgVectors<V> &e, const CgState &st, cudaStream_t s)
 {
     const int64_t nt = M.off[M.levels];
-    spmv<V, 0>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
     if (M.xfuse) {
+        // the matvec without reductions, p.q by a streaming pass (cheaper
+        // than the matvec's own epilogue for L_H)
+        spmv<V, 2>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
+        h.launches += 1;
+        k_pq<V><<<grid_for(h, nt / 4 + 1), kBlock, 0, s>>>(nt, e.p, e.q, st.sc, st.part, st.ticket);
         const size_t nb = M.band_t.size();
         h.launches += static_cast<int64_t>(2 * nb + 1);
         for (size_t b = 0; b < nb; ++b) {
@@ -859,6 +863,7 @@ void inner_iteration(const lap_handle_s &h, const DevCsr<V> &H, const DevMsp<V> 
         pupdate<V>(h, nt, e.Y, e.p, st, s);
         return;
     }
+    spmv<V, 0>(h, H, h.tprH, e.p, e.q, nullptr, nullptr, st, s);
     h.launches += 2;
     k_update<V, true, false><<<grid_for(h, nt), kBlock, 0, s>>>(static_cast<int>(nt), e.x, e.r, e.p,
                                                                 e.q, e.A, st.sc, st.part, st.ticket);

@@ -820,6 +820,36 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int stop;
+    V *sa = reinterpret_cast<V *>(smem_raw + P.sa_s);
+    V *sz = reinterpret_cast<V *>(smem_raw + P.sz_s);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    // the copies first: they do not depend on the step below
+    if (tid == 0) {
+        stop = 0;
+        const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const int a0_bytes = (P.a0_head + P.n0 * (int)sizeof(V) + 15) & ~15;
+        uint32_t tx = a0_bytes;
+        for (int k = 0; k < P.nlev; ++k) tx += P.lev[k].seg_b + P.lev[k].inv_b + P.lev[k].lcf_b;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(tx) : "memory");
+        auto copy = [&](int dst, const void *src, int bytes) {
+            if (bytes <= 0) return;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw + dst))),
+                "l"(src), "r"(bytes), "r"(b)
+                : "memory");
+        };
+        copy(P.sa_s - P.a0_head, reinterpret_cast<const unsigned char *>(P.A + P.off0) - P.a0_head, a0_bytes);
+        for (int k = 0; k < P.nlev; ++k) {
+            const TailLevel<V> &L = P.lev[k];
+            copy(L.seg_s, L.seg, L.seg_b);
+            copy(L.inv_s, L.inv, L.inv_b);
+            copy(L.lcf_s, L.lcf, L.lcf_b);
+        }
+    }
     if (P.fin) {
         // the first band's partials, summed in block order
         double v[2] = {0.0, 0.0};
@@ -845,6 +875,9 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
                         rv[k] = P.cr[b0 + i];
                     }
                 }
+                // the four values and squares summed in V, then in FP64
+                // (one SM's FP64 rate would dominate this block otherwise)
+                V r2 = V(0), r1s = V(0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int i = i0 + k * (int)blockDim.x;
@@ -852,10 +885,12 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
                         P.cx[b0 + i] = xv[k] + al * pv[k];
                         const V r1 = rv[k] - al * qv[k];
                         P.cr[b0 + i] = r1;
-                        v[0] += (double)r1 * (double)r1;
-                        v[1] += (double)r1;
+                        r2 += r1 * r1;
+                        r1s += r1;
                     }
                 }
+                v[0] += (double)r2;
+                v[1] += (double)r1s;
             }
         }
         block_sum<2>(v);
@@ -866,36 +901,6 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
                 finish_step(sc, v[0]);
             }
             stop = sc->flag != kRun;
-        }
-        __syncthreads();
-        if (stop) return;
-    }
-    V *sa = reinterpret_cast<V *>(smem_raw + P.sa_s);
-    V *sz = reinterpret_cast<V *>(smem_raw + P.sz_s);
-    const int tid = threadIdx.x, nth = blockDim.x;
-    if (tid == 0) {
-        const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        const int a0_bytes = (P.a0_head + P.n0 * (int)sizeof(V) + 15) & ~15;
-        uint32_t tx = a0_bytes;
-        for (int k = 0; k < P.nlev; ++k) tx += P.lev[k].seg_b + P.lev[k].inv_b + P.lev[k].lcf_b;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(tx) : "memory");
-        auto copy = [&](int dst, const void *src, int bytes) {
-            if (bytes <= 0) return;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                    static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw + dst))),
-                "l"(src), "r"(bytes), "r"(b)
-                : "memory");
-        };
-        copy(P.sa_s - P.a0_head, reinterpret_cast<const unsigned char *>(P.A + P.off0) - P.a0_head, a0_bytes);
-        for (int k = 0; k < P.nlev; ++k) {
-            const TailLevel<V> &L = P.lev[k];
-            copy(L.seg_s, L.seg, L.seg_b);
-            copy(L.inv_s, L.inv, L.inv_b);
-            copy(L.lcf_s, L.lcf, L.lcf_b);
         }
     }
     __syncthreads();
@@ -916,12 +921,34 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
             }
         }
     }
+    if (stop) return;                                   // converged: nothing to apply
+    if (P.fin == 3) {
+        // the updated r of the levels above the first, staged where the
+        // elimination adds it (after the copies have landed)
+        const int nup = P.ntail - P.n0;
+        for (int i0 = tid; i0 < nup; i0 += 8 * nth) {
+            V rv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * nth;
+                if (i < nup) rv[k] = P.cr[P.off0 + P.n0 + i];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * nth;
+                if (i < nup) sa[P.n0 + i] = rv[k];
+            }
+        }
+        __syncthreads();
+    }
     for (int k = 0; k < P.nlev; ++k) {
         const TailLevel<V> &L = P.lev[k];
         const int nloc = (k + 1 < P.nlev) ? P.lev[k + 1].loc : P.loc_top;
+        // fin 3: a_{k+1} = gamma sum + (staged r_{k+1}) in place
         elim_level(sa + L.loc, sa + nloc, reinterpret_cast<const int *>(smem_raw + L.seg_s), 0,
                    reinterpret_cast<const V *>(smem_raw + L.inv_s), reinterpret_cast<const V *>(smem_raw + L.lcf_s),
-                   L.gamma, P.F, P.off0 + nloc, L.nagg, 0, nth);
+                   L.gamma, P.fin == 3 ? static_cast<const V *>(sa + nloc) : P.F, P.fin == 3 ? 0 : P.off0 + nloc,
+                   L.nagg, 0, nth);
         __syncthreads();
     }
     {   // top: dense pseudo-inverse, one warp per row
@@ -955,15 +982,18 @@ k_msp_tail(const TailParams<V> P, CgScalars *sc)
                 const int i = i0 + k * nth;
                 if (i < P.ntail) rv[k] = P.cr[P.off0 + i];
             }
+            V a1 = V(0), a2 = V(0);             // eight terms in V, then FP64
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int i = i0 + k * nth;
                 if (i < P.ntail) {
-                    const double zv = (double)sz[i];
-                    v[0] += zv;
-                    v[1] += (double)rv[k] * zv;
+                    const V zv = sz[i];
+                    a1 += zv;
+                    a2 += rv[k] * zv;
                 }
             }
+            v[0] += (double)a1;
+            v[1] += (double)a2;
         }
         block_sum<2>(v);
         if (tid == 0) {
@@ -1036,6 +1066,43 @@ k_dense_z(int n, const double *__restrict__ G, const V *__restrict__ r, const V 
     if (grid_sum<3>(v, part, ticket) && threadIdx.x == 0) {
         const double m = v[0] / (double)n;
         set_direction(sc, m, v[1] - m * sc->rs, v[2]);
+    }
+}
+
+// p.q and sum q of a direction p and its product q = A p, and the step length
+// alpha = rho / p.q (as the matvec's MODE 0 epilogue, for a matvec launched
+// without reductions): groups of four in V, then FP64.
+template <typename V>
+__global__ void __launch_bounds__(kBlock)
+k_pq(int64_t n, const V *__restrict__ p, const V *__restrict__ q, CgScalars *sc, double *part, unsigned *ticket)
+{
+    if (halted(sc)) return;
+    double a0 = 0.0, a1 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        V pv[4], qv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * stride;
+            pv[k] = i < n ? p[i] : V(0);
+            qv[k] = i < n ? q[i] : V(0);
+        }
+        V s0 = V(0), s1 = V(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            s0 += pv[k] * qv[k];
+            s1 += qv[k];
+        }
+        a0 += (double)s0;
+        a1 += (double)s1;
+    }
+    double v[2] = {a0, a1};
+    if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
+        sc->pq = v[0];
+        sc->qsum = v[1];
+        const double alpha = sc->rho / v[0];
+        if (!(v[0] > 0.0) || !isfinite(alpha)) sc->flag = kBreakdown;
+        sc->alpha = alpha;
     }
 }
 

@@ -959,6 +959,49 @@ void outer_iteration(const lap_handle_s &h, cudaStream_t s)
     pupdate<V>(h, Sel<V>::M(h).off[1], is_plain(h) ? w.r : w.z, w.p, st, s);
 }
 
+// PEGP inner solves with at most this many iterations are sequenced on the
+// device: the outer iteration needs no host poll and is captured in a graph.
+constexpr int kDevInnerMax = 32;
+
+bool device_sequenced_pegp(const lap_handle_s &h)
+{
+    return is_pegp(h) && h.m.opt.inner_maxit <= kDevInnerMax && h.M64.levels > 1;
+}
+
+// One outer PEGP_inner iteration sequenced entirely on the device: the outer
+// step and its convergence test, r~ = P(mu)^T r, the inner CG on L_H run to
+// its cap (iterations after its own convergence return at once, and the
+// whole inner solve is stopped before it starts when the outer CG is not
+// running), its iteration count tallied, z = Pi P(mu) y~ with the outer
+// reductions, and the new direction.  Every kernel after the outer step
+// checks a flag, so check_every iterations are captured as one graph.
+template <typename V>
+void outer_pegp_iteration(const lap_handle_s &h, cudaStream_t s)
+{
+    const auto &w = Sel<V>::w(h);
+    const auto &st = Sel<V>::st(h);
+    const auto &M = Sel<V>::M(h);
+    const auto &e = Sel<V>::e(h);
+    const auto &ste = Sel<V>::ste(h);
+    const int64_t n = M.off[1], nt = M.off[M.levels];
+    spmv<V, 0>(h, Sel<V>::L(h), h.tpr, w.p, w.q, nullptr, nullptr, st, s);
+    h.launches += 3;
+    k_update<V, true, false><<<grid_for(h, n), kBlock, 0, s>>>(static_cast<int>(n), w.x, w.r, w.p, w.q, nullptr,
+                                                               st.sc, st.part, st.ticket);
+    restrict_tilde<V>(h, M, w.r, e.r, e.A, e.T, st.sc, s);
+    k_inner_reset<<<1, 1, 0, s>>>(ste.sc, st.sc, h.m.opt.inner_tol, h.m.opt.inner_maxit);
+    k_vec_init<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.r, e.x, ste.sc, ste.part, ste.ticket);
+    msp_tilde<V>(h, M, e.A, e.Y, ste.sc, s);
+    h.launches += 1;
+    k_zred<V><<<grid_for(h, nt), kBlock, 0, s>>>(nt, e.Y, e.r, ste.sc, ste.part, ste.ticket);
+    pupdate<V>(h, nt, e.Y, e.p, ste, s);
+    for (int i = 0; i < h.m.opt.inner_maxit; ++i) inner_iteration<V>(h, Sel<V>::H(h), M, e, ste, s);
+    h.launches += 1;
+    k_inner_tally<<<1, 1, 0, s>>>(ste.sc, st.sc);
+    prolong_tilde_to_z<V>(h, M, e.x, e.T, w, st, s);
+    pupdate<V>(h, n, w.z, w.p, st, s);
+}
+
 template <typename Fn>
 lap_status capture(lap_handle_s &h, cudaGraphExec_t &g, int64_t &nodes, Fn body)
 {
@@ -1064,7 +1107,8 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
     const auto &w = Sel<V>::w(h);
     const auto &st = Sel<V>::st(h);
     const int64_t n = Sel<V>::M(h).off[1];
-    if (is_pegp(h)) {
+    const bool dev_pegp = device_sequenced_pegp(h);
+    if (is_pegp(h) && !dev_pegp) {
         for (int guard = 0; guard <= h.m.opt.maxit + 4; ++guard) {
             spmv<V, 0>(h, Sel<V>::L(h), h.tpr, w.p, w.q, nullptr, nullptr, st, s);
             LAP_TRY(apply_precond<V>(h, true, t0, inner_total));
@@ -1077,8 +1121,27 @@ lap_status iterate(lap_handle_s &h, Clock::time_point t0, int &inner_total, CgSc
     }
     cudaGraphExec_t &g = Sel<V>::gi(h);
     if (!g) LAP_TRY(capture(h, g, Sel<V>::ni(h), [&] {
-            for (int i = 0; i < h.m.opt.check_every; ++i) outer_iteration<V>(h, s);
+            for (int i = 0; i < h.m.opt.check_every; ++i) {
+                if (dev_pegp) outer_pegp_iteration<V>(h, s);
+                else outer_iteration<V>(h, s);
+            }
         }));
+    int tally0 = 0;
+    if (dev_pegp) {
+        CgScalars s0;
+        LAP_TRY(poll(h, st, s0));
+        tally0 = s0.inner_total;
+    }
+    struct Tally {
+        bool on;
+        int base;
+        int &total;
+        const CgScalars &sc;
+        ~Tally()
+        {
+            if (on) total += sc.inner_total - base;
+        }
+    } tally{dev_pegp, tally0, inner_total, sc};
     // the device stops at maxit; the launch cap only guards the host loop
     const int cap = h.m.opt.maxit / h.m.opt.check_every + 4;
     // stall detection (mixed precision inner solves only): stop once the
@@ -1767,7 +1830,9 @@ lap_status update_options(lap_handle_s &h, const lap_options &o)
         h.hist_capacity = o.maxit;
         h.hist_count = h.lz_run = 0;
     }
-    if (o.check_every != cur.check_every) {
+    // the graphs hold the iteration counts (and the device-sequenced PEGP
+    // outer iterations the inner solve's tolerance and cap)
+    if (o.check_every != cur.check_every || o.inner_tol != cur.inner_tol || o.inner_maxit != cur.inner_maxit) {
         for (cudaGraphExec_t *g : {&h.g_iter64, &h.g_iter32, &h.g_in64, &h.g_in32})
             if (*g) {
                 cudaGraphExecDestroy(*g);

@@ -48,6 +48,7 @@ struct CgScalars {
     double *hist;      // optional recurrence-residual history (device), or null
     double *lz;        // optional (alpha, beta) of every step, 2 * hist_cap, or null
     int stop;          // FGMRES: the flag that ended the latest cycle
+    int inner_total;   // inner iterations of the device-sequenced PEGP solves
 };
 
 enum : int { kRun = 0, kConverged = 1, kBreakdown = 2, kMaxit = 3 };
@@ -1204,17 +1205,29 @@ k_gather(int n, const int *__restrict__ perm, const double *__restrict__ in, V *
 }
 
 // x = 0; reduce ||r||^2, sum r -> bnorm, rr, rs; start a CG (expanded-space inner solve)
+// (a stopped CG, e.g. gated by k_inner_reset, is left as it is)
 template <typename V>
 __global__ void __launch_bounds__(kBlock)
 k_vec_init(int64_t n, const V *__restrict__ r, V *__restrict__ x, CgScalars *sc, double *part,
            unsigned *ticket)
 {
+    if (halted(sc)) return;
     double s2 = 0.0, s1 = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)r[i];
-        x[i] = V(0);
-        s2 += v * v;
-        s1 += v;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        V a2 = V(0), a1 = V(0);            // groups of four in V, then FP64
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * stride;
+            if (i < n) {
+                const V v = r[i];
+                x[i] = V(0);
+                a2 += v * v;
+                a1 += v;
+            }
+        }
+        s2 += (double)a2;
+        s1 += (double)a1;
     }
     double v[2] = {s2, s1};
     if (grid_sum<2>(v, part, ticket) && threadIdx.x == 0) {
@@ -1253,6 +1266,7 @@ k_zred(int64_t n, const V *__restrict__ z, const V *__restrict__ r, CgScalars *s
 static __global__ void k_cg_reset(CgScalars *sc, double tol, int maxit, int flexible, double *hist,
                                   int hist_cap, double *lz = nullptr)
 {
+    sc->inner_total = 0;
     sc->tol = tol;
     sc->maxit = maxit;
     sc->flexible = flexible;
@@ -1295,6 +1309,29 @@ static __global__ void k_bench_scalars(CgScalars *sc)
     sc->hist = nullptr;
     sc->hist_cap = 0;
     sc->lz = nullptr;
+}
+
+// Start of a PEGP inner solve sequenced on the device: the inner CG's
+// bookkeeping as k_cg_reset, already stopped if the outer CG is not running
+// (its step just converged, broke down or reached maxit), so that the whole
+// inner solve and the prolongation after it return at once.
+static __global__ void k_inner_reset(CgScalars *inner, const CgScalars *outer, double tol, int maxit)
+{
+    inner->tol = tol;
+    inner->maxit = maxit;
+    inner->flexible = 0;
+    inner->iter = 0;
+    inner->first = 1;
+    inner->hist = nullptr;
+    inner->hist_cap = 0;
+    inner->lz = nullptr;
+    inner->flag = outer->flag == kRun ? kRun : kConverged;
+}
+
+// The inner solve's iterations added to the outer CG's tally.
+static __global__ void k_inner_tally(const CgScalars *inner, CgScalars *outer)
+{
+    if (outer->flag == kRun) outer->inner_total += inner->iter;
 }
 
 static __global__ void k_cg_restart(CgScalars *sc)

@@ -372,6 +372,40 @@ lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, const int32_t
                                  lap_solve_info *infos);
 
 /*
+ * Solve groups: many graphs of uneven size solved together with one launch
+ * per PCG phase for all of them (the scope table's batched row: graphs
+ * concatenated block-diagonally with per-graph segment ids and per-(graph,
+ * column) CG scalars; the paper solves one system at a time, Section 4).
+ *
+ * lap_group_create merges the setups of ng handles (caller-owned; they must
+ * outlive the group, which uses their top-level dense pseudo-inverses in
+ * place): all with LAP_PREC_MSP or all with LAP_PREC_NONE (else
+ * LAP_ERR_UNSUPPORTED; the PEGP preconditioners are refused: their inner
+ * solves on L_H run per graph), every hierarchy with at least two levels
+ * (LAP_ERR_UNSUPPORTED), the same precision, mu and device
+ * (LAP_ERR_INVALID_ARG).  The merge copies the graphs' level-1 Laplacians,
+ * aggregation segments and elimination coefficients into one block-diagonal
+ * layout on the device (graphs ordered by decreasing hierarchy depth); the
+ * solve options (tol, maxit, check_every, refinement) are the first
+ * handle's at creation.
+ *
+ * lap_pcg_solve_group solves graph g's nrhs[g] (0..256) right-hand sides
+ * d_B[g] (column-major, n_g x nrhs[g], device) into d_X[g] (same layout) on
+ * `stream`, every (graph, column) pair with its own CG (and, with
+ * LAP_MIXED, its own FP64 refinement), stopping on its own.  Each PCG phase
+ * (matvec, each sweep level, the graphs' top-level solves, the direction
+ * update) is one launch over all graphs; the iterations run as CUDA graphs
+ * of check_every steps.  infos (optional, host) receives sum(nrhs) entries in
+ * (graph, column) order.  Reuses its workspace between calls of the same
+ * maximum width; one call at a time per group.
+ */
+typedef struct lap_group_s *lap_group;
+lap_status lap_group_create(int32_t ng, const lap_handle *hs, lap_group *out);
+lap_status lap_pcg_solve_group(lap_group grp, const int32_t *nrhs, const double *const *d_B,
+                               double *const *d_X, void *stream, lap_solve_info *infos);
+void lap_group_destroy(lap_group grp);
+
+/*
  * Residual of a graph Laplacian system without any device allocation.
  *
  * The paper has no counterpart to this entry point; it exists for callers

@@ -106,6 +106,9 @@ SIGNATURES = [
     ("lap_pcg_solve_batched", _I32, [_I32, _VP, _VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
     ("lap_laplacian_residual_noalloc", _I32, [_I64, _VP, _VP, _VP, _VP, _VP, _VP,
                                                C.POINTER(_D), _VP]),
+    ("lap_group_create", _I32, [_I32, _VP, C.POINTER(_VP)]),
+    ("lap_pcg_solve_group", _I32, [_VP, _VP, _VP, _VP, _VP, C.POINTER(lap_solve_info)]),
+    ("lap_group_destroy", None, [_VP]),
     ("lap_server_options_default", None, [C.POINTER(lap_server_options)]),
     ("lap_server_create", _I32, [C.POINTER(lap_server_options), C.POINTER(_VP)]),
     ("lap_serve_submit", _I32, [_VP, _VP, _I32, _VP, _VP, LAP_DONE_CB, _VP, C.POINTER(_U64)]),
@@ -391,6 +394,43 @@ def lap_pcg_solve_batched(handles, Bs, Xs, stream=None):
     infos = (lap_solve_info * tot)()
     st = lib().lap_pcg_solve_batched(ng, hs, nr, pb, px, _stream(stream), infos)
     return st, list(infos)
+
+
+class Group:
+    """A solve group (lap_group_create): the handles' graphs merged for
+    solves with one launch per PCG phase for all of them.  Keeps the handles
+    alive as long as the group."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        ng = len(self.handles)
+        hs = (C.c_void_p * ng)(*[h.ptr for h in self.handles])
+        p = C.c_void_p()
+        _check(lib().lap_group_create(ng, hs, C.byref(p)), "lap_group_create")
+        self.ptr = p.value
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().lap_group_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lap_pcg_solve_group(group, Bs, Xs, stream=None):
+    """Group solve: graph g's right-hand sides Bs[g] ((nrhs_g, n_g) row-major
+    = n_g x nrhs_g column-major) into Xs[g]; (status, infos)."""
+    ng = len(group.handles)
+    nr = (C.c_int32 * ng)(*[int(B.shape[0]) if B.dim() == 2 else 1 for B in Bs])
+    pb = (C.c_void_p * ng)(*[_ptr(B) for B in Bs])
+    px = (C.c_void_p * ng)(*[_ptr(X) for X in Xs])
+    infos = (lap_solve_info * max(sum(nr), 1))()
+    st = lib().lap_pcg_solve_group(group.ptr, nr, pb, px, _stream(stream), infos)
+    return st, list(infos)[:sum(nr)]
 
 
 def lap_laplacian_residual_noalloc(row_ptr, col_idx, w, x, b, r, stream=None):

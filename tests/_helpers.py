@@ -62,6 +62,24 @@ PARITY_GRAPHS = {
 }
 
 
+# The graphs of the GPU group-solve test (tests/test_gpu_group.py): uneven
+# sizes from 1.5e2 to 1e5 vertices, several families, each with its own
+# number of right-hand sides; the right-hand sides of graph g are
+# gg.rhs(n, seed=100 + 10 g + j), j < nrhs.
+GROUP_GRAPHS = [
+    ("path_150", lambda: gg.path(150, w=np.linspace(1, 3, 149)), 3),
+    ("grid2d_20x17", lambda: gg.grid2d(20, 17, weights="uniform", lo=1.0, hi=2.0, seed=11), 1),
+    ("rgg_1200", lambda: gg.rgg(1200, seed=12), 5),
+    ("chunglu_3000", lambda: gg.chung_lu(3000, avg_deg=12, seed=13), 16),
+    ("grid3d_16x15x14", lambda: gg.grid3d(16, 15, 14, weights="loguniform", lo=1e-3, hi=1e3, seed=14), 2),
+    ("ring_9000", lambda: gg.ring(9000, 2, weights="uniform", seed=15), 7),
+    ("grid2d_160x150", lambda: gg.grid2d(160, 150, weights="loguniform", lo=1e-2, hi=1e2, seed=16), 4),
+    ("rmat_14", lambda: gg.rmat(14, 16, seed=17), 9),
+    ("grid3d_40", lambda: gg.grid3d(40, weights="uniform", lo=1.0, hi=2.0, seed=18), 1),
+    ("grid2d_320x310", lambda: gg.grid2d(320, 310, weights="uniform", lo=1.0, hi=2.0, seed=19), 3),
+]
+
+
 def hub_graph():
     """Six hubs in a path, each with its own leaves (2,500, 2,500, 8,000,
     8,000, 300 and 300): every hub's aggregate holds all its leaves, so the
@@ -109,6 +127,12 @@ ITER_SPREAD = {
     ("batched_grid3d_18", "none", 0): 14,
     ("batched_grid3d_18", "none", 5): 3,
     ("served_grid2d_56x40", "msp"): 7,
+    # column 0 of the group-solve graphs
+    ("group", "grid3d_16x15x14"): 8,
+    ("group", "ring_9000"): 6,
+    ("group", "grid2d_160x150"): 16,
+    ("group", "grid3d_40"): 2,
+    ("group", "grid2d_320x310"): 5,
 }
 
 

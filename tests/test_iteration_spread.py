@@ -31,8 +31,8 @@ import oracle
 from oracle.expanded import expanded_operators
 from oracle.solve import OraclePreconditioner, _GroundedSolver, fgmres, pcg
 
-from _helpers import (ITER_SPREAD, PARITY_GRAPHS, GroundedLU, PerturbedSolve, RoundedProduct,
-                      hub_graph, reversed_csr)
+from _helpers import (GROUP_GRAPHS, ITER_SPREAD, PARITY_GRAPHS, GroundedLU, PerturbedSolve,
+                      RoundedProduct, hub_graph, reversed_csr)
 
 PERTURBED_RUNS = 3
 _POOL = None
@@ -200,3 +200,12 @@ def test_spread_of_the_exact_pegp_cases(mu):
     g = PARITY_GRAPHS["grid2d_64"]()
     spread, counts = _spread(g, "pegp_exact", gg.rhs(g.n, seed=2), mu=mu)
     _check(("grid2d_64", "pegp_exact", mu), spread, counts)
+
+
+@pytest.mark.parametrize("idx", range(len(GROUP_GRAPHS)))
+def test_spread_of_the_group_cases(idx):
+    """Column 0 of each graph of the group-solve test."""
+    name, make, _ = GROUP_GRAPHS[idx]
+    g = make()
+    spread, counts = _spread(g, "msp", gg.rhs(g.n, seed=100 + 10 * idx))
+    _check(("group", name), spread, counts)

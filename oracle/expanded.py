@@ -61,11 +61,15 @@ def composite_prolongation(h: Hierarchy, mu: float) -> sp.csr_matrix:
 
 
 def _upper_entries(m: sp.spmatrix):
-    c = sp.triu(m, k=1, format="coo")
-    c.sum_duplicates()
-    r, q, v = c.row.astype(np.int64), c.col.astype(np.int64), c.data
-    order = np.lexsort((q, r))
-    return r[order], q[order], v[order]
+    """Strictly upper entries (row, col, value) of m, sorted by (row, col).
+    In canonical CSR (sorted indices, duplicates summed) they already come
+    in that order, so they are picked out without sorting."""
+    m = sp.csr_matrix(m)
+    m.sum_duplicates()                               # canonical: sorted, no duplicates
+    rows = np.repeat(np.arange(m.shape[0], dtype=np.int64), np.diff(m.indptr))
+    cols = m.indices.astype(np.int64)
+    keep = cols > rows
+    return rows[keep], cols[keep], m.data[keep]
 
 
 def _from_upper(nt: int, i, j, wgt) -> sp.csr_matrix:

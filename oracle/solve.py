@@ -158,12 +158,16 @@ class SolveResult:
     betas: list = field(default_factory=list)    # direction coefficients of that run
 
 
-def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=False) -> SolveResult:
+def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=False,
+        deadline=None) -> SolveResult:
     """Preconditioned CG on the singular consistent system L x = Pi b, x_0 = 0.
 
     beta = r_k^T z_k / r_{k-1}^T z_{k-1} (standard) or, if flexible,
     beta = z_k^T (r_k - r_{k-1}) / r_{k-1}^T z_{k-1} (FCG(1), Notay 2000).
-    L is a sparse matrix or any operator whose product is ``L @ v``."""
+    L is a sparse matrix or any operator whose product is ``L @ v``.
+    deadline (a time.perf_counter() value, optional) ends the iteration after
+    the first step completed past it (timing runs; not converged)."""
+    import time
     L = sp.csr_matrix(L) if sp.issparse(L) else L
     bp = _project(np.asarray(b, dtype=np.float64))
     nb = np.linalg.norm(bp)
@@ -189,6 +193,8 @@ def pcg(L: sp.spmatrix, b: np.ndarray, M, *, tol=1e-8, maxit=1000, flexible=Fals
         its += 1
         rel = np.linalg.norm(r) / nb
         hist.append(rel)
+        if deadline is not None and time.perf_counter() > deadline:
+            break
         if rel <= tol:
             rt = bp - L @ x
             if np.linalg.norm(rt) / nb <= tol:

@@ -435,3 +435,23 @@ def test_pegp_exact_few_iterations_on_grids():
     g = gg.grid2d(32, weights="uniform", lo=1.0, hi=2.0, seed=1)
     res = oracle.solve(g, gg.rhs(g.n, seed=2), "pegp_exact", mu=1 / 32, seed=1)
     assert res.converged and res.iters <= 8
+
+
+def test_upper_entries_equal_the_sorted_triangle():
+    """The oracle's strictly-upper entry list equals the sorted upper triangle
+    (duplicates summed) of the same matrix, entry by entry."""
+    import scipy.sparse as sp
+    from oracle.expanded import _upper_entries
+    rng = np.random.default_rng(3)
+    for n in (1, 7, 300):
+        i = rng.integers(0, n, 5 * n)
+        j = rng.integers(0, n, 5 * n)
+        v = rng.standard_normal(5 * n)
+        m = sp.coo_matrix((v, (i, j)), shape=(n, n))          # with duplicates
+        r, q, w = _upper_entries(m.tocsr())
+        c = sp.triu(m, k=1, format="coo")
+        c.sum_duplicates()
+        order = np.lexsort((c.col, c.row))
+        np.testing.assert_array_equal(r, c.row[order])
+        np.testing.assert_array_equal(q, c.col[order])
+        np.testing.assert_array_equal(w, c.data[order])

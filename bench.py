@@ -20,6 +20,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,7 +37,6 @@ WORKLOAD = {
     "nx": 128, "wlo": 1e-3, "whi": 1e3, "wseed": 3, "prec": "pegp_inner", "mu": 0.8,
     "tol": 1e-8, "inner_tol": 1e-1, "inner_maxit": 12, "setup_seed": 1,
 }
-CPU_SAMPLE_NX = {"pegp_inner": 16, "pegp_exact": 16, "msp": 24, "none": 24}   # oracle sample sides
 FP64_ALU_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (no measured figure exists)
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current
 # kernel, scaled to the 128^3 workload (profiles/k_sell_f32_LH_grid3d96.md);
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--aux-steps", type=int, default=1,
+    ap.add_argument("--aux-steps", type=int, default=5,
                     help="timed solves of the FP64 comparison, e2e and MSP lines")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling run: one solve of each kind capped at this many outer "
@@ -76,6 +76,12 @@ def parse():
     ap.add_argument("--handshake", type=int, default=1,
                     help="1: also solve the headline grid with the deterministic parallel "
                          "matching variant (a method change; reported apart, 0: skip)")
+    ap.add_argument("--group-graphs", type=int, default=16,
+                    help="graphs of the solve-group line (0: skip)")
+    ap.add_argument("--oracle-cap-s", type=float, default=40.0,
+                    help="seconds of timed oracle iterations per oracle leg")
+    ap.add_argument("--sweep-inner", action="store_true",
+                    help="only sweep the PEGP inner cap and tolerance at the workload")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -157,56 +163,205 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+REF_OUTER_ITERATIONS = 2000   # outer iterations per solve assumed by the reference arm (see DESIGN)
+
+
+def host_description():
+    """CPU model and logical core count of this host."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "processor\t")) and ":" in ln:
+                    v = ln.split(":", 1)[1].strip()
+                    if ln.lower().startswith("model name") and v:
+                        model = v
+                        break
+    except OSError:
+        pass
+    try:
+        import subprocess as sp_
+        out = sp_.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "machine": platform.machine()}
+
+
 def oracle_worker(spec_json):
-    """Runs in a single-threaded subprocess: the oracle solve on the sample."""
+    """Runs in its own process.  mode "capped": build the oracle preconditioner
+    of the full workload (setup, not timed), report ready, optionally wait
+    for a line on stdin, then run the oracle PCG for cap_s seconds and report
+    the outer iterations completed (and their inner iterations).  mode
+    "samples": oracle solutions of the reduced error-check systems, saved to
+    spec["out"]."""
     spec = json.loads(spec_json)
     import numpy as np
 
     import graphgen as gg
     import oracle
-    g = gg.grid3d(spec["nx"], weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
-                  seed=WORKLOAD["wseed"])
-    M = oracle.make_preconditioner(spec["prec"], g, mu=WORKLOAD["mu"], seed=WORKLOAD["setup_seed"],
-                                   inner_tol=WORKLOAD["inner_tol"],
-                                   inner_maxit=WORKLOAD["inner_maxit"])
-    from oracle.solve import _laplacian_of
-    L = M.ops.L if M.ops is not None else _laplacian_of(g)
-    times, work = [], []
-    for i in range(spec["reps"]):
-        b = gg.rhs(g.n, seed=100 + i)
-        M.inner_iters.clear()
-        t0 = time.perf_counter()
-        res = oracle.pcg(L, b, M, tol=WORKLOAD["tol"], maxit=5000, flexible=M.flexible)
-        times.append(time.perf_counter() - t0)
-        work.append(res.iters + sum(M.inner_iters))
-        assert res.converged
-    print(json.dumps({"n": g.n, "times": times, "work": work}))
+    if spec["mode"] == "samples":
+        sols = {}
+        for name, (kind, g, mu, kw, seeds) in error_samples().items():
+            for s_ in seeds:
+                b = gg.rhs(g.n, seed=s_)
+                res = oracle.solve(g, b, kind, mu=mu, seed=WORKLOAD["setup_seed"], maxit=20000, **kw)
+                sols[f"{name}:{s_}"] = res.x
+        np.savez(spec["out"], **sols)
+        print(json.dumps({"done": len(sols)}), flush=True)
+        return
+    nx = spec["nx"]
+    g = gg.grid3d(nx, weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"], seed=WORKLOAD["wseed"])
+    t0 = time.perf_counter()
+    ho = oracle.build_hierarchy(g.row_ptr, g.col_idx, g.w, seed=WORKLOAD["setup_seed"])
+    ops = oracle.expanded_operators(ho, WORKLOAD["mu"], with_LG=False)
+    M = oracle.OraclePreconditioner(spec["prec"], ops, inner_tol=WORKLOAD["inner_tol"],
+                                    inner_maxit=WORKLOAD["inner_maxit"])
+    L = ops.L
+    setup_s = time.perf_counter() - t0
+    print(json.dumps({"ready": True, "setup_s": setup_s, "n": g.n}), flush=True)
+    if spec.get("wait"):
+        sys.stdin.readline()
+    b = gg.rhs(g.n, seed=100)
+    t0 = time.perf_counter()
+    res = oracle.pcg(L, b, M, tol=WORKLOAD["tol"], maxit=10 ** 6, flexible=M.flexible,
+                     deadline=t0 + spec["cap_s"])
+    t = time.perf_counter() - t0
+    print(json.dumps({"n": g.n, "outer": res.iters, "inner": int(sum(M.inner_iters)), "seconds": t,
+                      "relres": res.history[-1] if res.history else 1.0, "setup_s": setup_s}), flush=True)
 
 
-def run_oracle(nx, prec, reps):
+_WORKERS = []
+
+
+def _kill_workers():
+    for p_ in _WORKERS:
+        if p_.poll() is None:
+            p_.kill()
+
+
+def start_oracle(nx, prec, cap_s, threads, wait):
+    """A capped oracle worker in its own process (setup starts at once)."""
+    th = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=th, OPENBLAS_NUM_THREADS=th, MKL_NUM_THREADS=th)
+    spec = json.dumps({"mode": "capped", "nx": nx, "prec": prec, "cap_s": cap_s, "wait": wait})
+    if not _WORKERS:
+        import atexit
+        atexit.register(_kill_workers)
+    p_ = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
+                          stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                          text=True, env=env)
+    _WORKERS.append(p_)
+    return p_
+
+
+def finish_oracle(proc, timeout=1800):
+    """Wait for the worker's setup, start its timed iterations, return its report."""
+    ready = json.loads(proc.stdout.readline() or "{}")
+    if not ready.get("ready"):
+        proc.kill()
+        raise RuntimeError("oracle worker failed: " + proc.stderr.read()[-1500:])
+    proc.stdin.write("go\n")
+    proc.stdin.flush()
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError(err[-1500:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def oracle_rate(rep, outer_per_solve):
+    """Solves/s of the oracle from its timed outer iterations at the full
+    workload and the outer iterations one solve takes."""
+    per_iter = rep["seconds"] / max(rep["outer"], 1)
+    return 1.0 / (per_iter * outer_per_solve), per_iter
+
+
+def cpu_baseline(procs, n_full, outer_per_solve, source):
+    """The oracle at the full workload, timed for a bounded number of outer
+    iterations, single-threaded and with every core for its BLAS."""
+    legs = {}
+    for threads, proc in procs:
+        rep = finish_oracle(proc)
+        rate, per_iter = oracle_rate(rep, outer_per_solve)
+        legs[threads] = (rate, per_iter, rep)
+    best = max(legs, key=lambda t: legs[t][0])
+    rate, per_iter, rep = legs[best]
+    hd = host_description()
+    desc = "; ".join(f"{t} thread(s): {l[2]['outer']} outer ({l[2]['inner']} inner) iterations in "
+                     f"{l[2]['seconds']:.1f} s, {l[1]:.2f} s per outer iteration, {l[0]:.3g} solves/s"
+                     for t, l in sorted(legs.items()))
+    return {"value": rate, "unit": "solves/s", "cores": best, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy PCG with the PEGP inner solve) on the full {n_full}-vertex "
+                       f"workload, setup excluded ({rep['setup_s']:.0f} s), timed for a bounded number "
+                       f"of outer iterations: {desc}; solves/s = 1 / (seconds per outer iteration x "
+                       f"{outer_per_solve} outer iterations per solve, {source})"),
+            "host": hd, "legs": {str(t): {"solves_per_s": l[0], "s_per_outer": l[1],
+                                          "outer": l[2]["outer"], "seconds": l[2]["seconds"]}
+                                 for t, l in legs.items()}}
+
+
+def error_samples():
+    """Reduced systems of each workload for the error against the FP64 oracle:
+    name -> (preconditioner, graph, mu, options, right-hand side seeds)."""
+    import graphgen as gg
+    return {
+        "grid2d_64_pegp_exact_fp64": ("pegp_exact", gg.grid2d(64, weights="uniform", lo=1.0, hi=2.0, seed=1),
+                                      1 / 64, {}, (900, 901)),
+        "grid3d_16_loguniform_pegp_inner_mixed": (
+            "pegp_inner", gg.grid3d(16, weights="loguniform", lo=1e-3, hi=1e3, seed=3), 0.8,
+            {"inner_tol": 0.1, "inner_maxit": 12}, (902,)),
+        "chunglu_16384_msp_mixed": ("msp", gg.chung_lu(1 << 14, avg_deg=16.0, gamma=2.5, weights="uniform01",
+                                                       seed=4), 0.8, {}, (903, 904)),
+        "rmat_s12_msp_mixed_batched": ("msp", gg.rmat(12, 16, seed=5), 0.8, {}, (905, 906, 907, 908)),
+    }
+
+
+def start_samples(path):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    spec = json.dumps({"nx": nx, "prec": prec, "reps": reps})
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
-                         capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    spec = json.dumps({"mode": "samples", "out": path})
+    p_ = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
+                          stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+    _WORKERS.append(p_)
+    return p_
 
 
-def cpu_baseline(prec, n_full, work_full, reps=1):
-    """Oracle solves/s on the 24^3 sample, scaled to the full workload by vertex
-    count and by (outer + inner) iterations per solve."""
-    nx = CPU_SAMPLE_NX[prec]
-    r = run_oracle(nx, prec, reps)
-    t = statistics.median(r["times"])
-    w = statistics.median(r["work"])
-    scaled = (1.0 / t) * (r["n"] * w) / (n_full * work_full)
-    return {"value": scaled, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (numpy/scipy, 1 thread) full solve of the same generator at "
-                       f"{nx}^3 = {r['n']} vertices: {t:.2f} s for {w} outer+inner "
-                       f"iterations; scaled by vertices and iterations to the {n_full}-vertex "
-                       f"workload at {work_full} iterations"),
-            "sample_solves_per_s": 1.0 / t}
+def errors_vs_oracle(proc, path, dev):
+    """||x_gpu - x_oracle|| / ||x_oracle|| on the reduced systems (GPU solves
+    through the C ABI; the oracle's FP64 solutions from the sample worker)."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+    out, err = proc.communicate(timeout=1800)
+    if proc.returncode != 0:
+        raise RuntimeError(err[-1500:])
+    ref = np.load(path)
+    res = {}
+    for name, (kind, g, mu, kw, seeds) in error_samples().items():
+        precision = "fp64" if name.endswith("fp64") else "mixed"
+        opts = {k: v for k, v in kw.items()}
+        h = P.lap_setup(g, prec=kind, mu=mu, precision=precision, seed=WORKLOAD["setup_seed"], maxit=20000,
+                        **opts)
+        B = torch.stack([torch.as_tensor(gg.rhs(g.n, seed=s_), device=dev) for s_ in seeds])
+        X = torch.empty_like(B)
+        if name.endswith("batched"):
+            st, infos = P.lap_pcg_solve_batched([h], [B], [X])
+        else:
+            infos = [P.lap_pcg_solve(h, B[j], X[j]) for j in range(len(seeds))]
+        torch.cuda.synchronize()
+        errs = []
+        for j, s_ in enumerate(seeds):
+            xo = ref[f"{name}:{s_}"]
+            errs.append(float(np.linalg.norm(X[j].cpu().numpy() - xo) / np.linalg.norm(xo)))
+        res[name] = {"n": g.n, "columns": len(seeds), "error_max": max(errs),
+                     "relres_max": max(i.relres for i in infos),
+                     "status": [i.status for i in infos]}
+        h.close()
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -229,8 +384,20 @@ def bench_ours(args, rank, world):
         raise SystemExit("--prec pegp_exact is for profiling runs (--profile); the exact PEGP "
                          "is timed on the small 2D grid line (--exact-side)")
 
+    # the oracle legs: their setups run on other host cores while the GPU is measured
+    oracle_procs, samples = [], None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile and not args.sweep_inner:
+        try:
+            oracle_procs = [(t, start_oracle(args.nx, args.prec, args.oracle_cap_s, t, True))
+                            for t in (1, os.cpu_count() or 1)]
+            path = os.path.join(tempfile.mkdtemp(), "oracle_samples.npz")
+            samples = (start_samples(path), path)
+        except Exception as e:
+            print(f"[bench] oracle legs not started: {e}", file=sys.stderr)
     g = gg.grid3d(args.nx, weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
                   seed=WORKLOAD["wseed"])
+    if args.sweep_inner:
+        return sweep_inner(args, g, dev)
     t0 = time.perf_counter()
     h = P.lap_setup(g, prec=args.prec, mu=WORKLOAD["mu"], precision="mixed",
                     seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"],
@@ -380,6 +547,8 @@ def bench_ours(args, rank, world):
         result["powerlaw"] = bench_powerlaw(args, dev, world)
     if args.batched_scale > 0:
         result["batched"] = bench_batched(args, dev, world)
+    if args.group_graphs > 0:
+        result["group"] = bench_group(args, dev, world)
     if args.serve_requests > 0:
         result["serving"] = bench_serving(args, dev, world)
     if args.handshake:
@@ -387,11 +556,18 @@ def bench_ours(args, rank, world):
             result["handshake_matching"] = bench_handshake(args, dev, world)
         except Exception as e:          # a variant line, never fatal to the report
             result["handshake_matching"] = {"error": str(e)[-300:]}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if oracle_procs:
         try:
-            result["cpu_baseline"] = cpu_baseline(args.prec, g.n, it_fp64 + inner_fp64)
+            result["cpu_baseline"] = cpu_baseline(
+                oracle_procs, g.n, it_fp64,
+                f"the median outer iterations of this run's FP64 arm on the GPU, the same iteration")
         except Exception as e:          # the baseline is reported, never fatal
             result["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    if samples:
+        try:
+            result["error_vs_oracle"] = errors_vs_oracle(samples[0], samples[1], dev)
+        except Exception as e:
+            result["error_vs_oracle"] = {"error": str(e)[-300:]}
     return result
 
 
@@ -580,6 +756,109 @@ def bench_batched(args, dev, world):
             "gen_s": round(gen_s, 2), "setup_s": round(setup_s, 2)}
 
 
+def bench_group(args, dev, world):
+    """Many graphs of uneven size at once: `group_graphs` graphs with vertex
+    counts log-uniform in [2e2, 1e5] (2D and 3D grids, Chung-Lu with mean
+    degree 8..32, random geometric graphs; weights log-uniform in [1e-2,
+    1e2]), each with 1..16 N(0,1) right-hand sides, MSP (mu = 0.8), mixed
+    precision: one solve group (one launch per PCG phase for all graphs)
+    against the same graphs solved one after another by the batched path."""
+    import numpy as np
+    import torch
+
+    import paper_2207_07847_gb300 as P
+    rng = np.random.default_rng(23)
+    G = args.group_graphs
+    sizes = np.exp(rng.uniform(math.log(2e2), math.log(1e5), G))
+    kinds = ["grid2d", "grid3d", "chung_lu", "rgg"]
+    graphs = [_serving_graph(kinds[i % 4], sizes[i], rng, 600 + i) for i in range(G)]
+    hs = [P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                      tol=WORKLOAD["tol"], maxit=20000) for g in graphs]
+    nr = rng.integers(1, 17, G)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(800)
+    Bs = [torch.randn(int(nr[i]), graphs[i].n, dtype=torch.float64, device=dev, generator=gen) for i in range(G)]
+    Xs = [torch.empty_like(b) for b in Bs]
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    grp = P.Group(hs)
+    create_s = time.perf_counter() - t0
+
+    def timed(fn):
+        fn()                                            # warm-up (graphs, workspaces)
+        ranks_barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ranks_barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1), world, dev), out
+
+    ms_g, (st, infos) = timed(lambda: P.lap_pcg_solve_group(grp, Bs, Xs))
+
+    def sequential():
+        allinf = []
+        for i in range(G):
+            st_, inf_ = P.lap_pcg_solve_batched([hs[i]], [Bs[i]], [Xs[i]])
+            allinf += inf_
+        return allinf
+
+    ms_s, inf_s = timed(sequential)
+    rhs = int(nr.sum())
+    its = sorted(i.iterations for i in infos)
+    out = {"workload": f"group_{G}graphs_n2e2..1e5_msp_mixed", "graphs": G,
+           "n_min": int(min(g.n for g in graphs)), "n_max": int(max(g.n for g in graphs)),
+           "n_total": int(sum(g.n for g in graphs)), "rhs": rhs,
+           "value": whole_job_rate(rhs, world, ms_g), "unit": "solves/s", "ms": ms_g,
+           "launches": int(infos[0].kernel_launches) if infos else 0,
+           "iterations": {"median": its[len(its) // 2], "max": its[-1]},
+           "relres_max": max(i.relres for i in infos), "failed": sum(1 for i in infos if i.status != 0),
+           "create_s": round(create_s, 3),
+           "graph_after_graph": {"value": whole_job_rate(rhs, world, ms_s), "unit": "solves/s", "ms": ms_s,
+                                 "launches": int(sum(i.kernel_launches for i in inf_s[:1]) if inf_s else 0),
+                                 "relres_max": max(i.relres for i in inf_s),
+                                 "failed": sum(1 for i in inf_s if i.status != 0)}}
+    grp.close()
+    for h in hs:
+        h.close()
+    return out
+
+
+def sweep_inner(args, g, dev):
+    """PEGP inner cap x inner tolerance at the workload: one mixed solve each
+    after a warm-up, solves/s and iterations (chooses the headline's settings)."""
+    import torch
+
+    import graphgen as gg
+    import paper_2207_07847_gb300 as P
+    h = P.lap_setup(g, prec="pegp_inner", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                    tol=WORKLOAD["tol"], inner_tol=0.1, inner_maxit=12, maxit=30000)
+    stream = torch.cuda.current_stream()
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    b0 = torch.as_tensor(gg.rhs(g.n, seed=100), device=dev)
+    b1 = torch.as_tensor(gg.rhs(g.n, seed=101), device=dev)
+    rows = []
+    for cap in (6, 12, 24):
+        for tol in (0.3, 0.1, 0.01):
+            P.lap_update_options(h, inner_maxit=cap, inner_tol=tol)
+            P.lap_pcg_solve(h, b0, x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = P.lap_pcg_solve(h, b1, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rows.append({"inner_maxit": cap, "inner_tol": tol, "solves_per_s": 1e3 / ms, "ms": ms,
+                         "outer": info.iterations, "inner": info.inner_iterations, "relres": info.relres,
+                         "status": info.status})
+            print(f"[sweep] {rows[-1]}", file=sys.stderr, flush=True)
+    h.close()
+    return {"sweep_inner": rows, "workload": WORKLOAD["name"]}
+
+
 def _serving_graph(kind, n, rng, seed):
     import graphgen as gg
     w = dict(weights="loguniform", lo=1e-2, hi=1e2, seed=seed)
@@ -740,34 +1019,31 @@ def bench_serving(args, dev, world):
 
 
 def bench_reference(args):
-    """The oracle as the reference arm: each step one full oracle solve of the
-    24^3 sample, reported in solves/s scaled to the 128^3 workload."""
-    import graphgen as gg
-    n_full = args.nx ** 3
-    reps = args.steps + args.warmup
-    nx = CPU_SAMPLE_NX[args.prec]
-    small = run_oracle(nx * 2 // 3, args.prec, 1)
-    r = run_oracle(nx, args.prec, reps)
-    times = r["times"][args.warmup:]
-    work = statistics.median(r["work"])
-    # iterations per solve at full size: power law in the grid side fitted to
-    # the two sample sizes (16^3 and 24^3)
-    expo = math.log(work / statistics.median(small["work"])) / math.log(1.5)
-    work_full = work * (args.nx / nx) ** expo
-    t = sum(times)
-    value = len(times) / t * (r["n"] * work) / (n_full * work_full)
-    return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+    """The oracle as the reference arm, by the same method as the cpu_baseline
+    leg: its PCG on the full workload (setup excluded), timed over the outer
+    iterations that fit args.oracle_cap_s seconds after args.warmup untimed
+    ones, single-threaded; solves/s = 1 / (seconds per outer iteration x
+    REF_OUTER_ITERATIONS).  A step is one outer iteration."""
+    cap = args.oracle_cap_s
+    proc = start_oracle(args.nx, args.prec, cap, 1, False)
+    rep = finish_oracle(proc)
+    rate, per_iter = oracle_rate(rep, REF_OUTER_ITERATIONS)
+    hd = host_description()
+    sample = (f"oracle (numpy/scipy PCG with the PEGP inner solve, 1 thread) on the full {rep['n']}-vertex "
+              f"workload, setup excluded ({rep['setup_s']:.0f} s): {rep['outer']} outer ({rep['inner']} inner) "
+              f"iterations in {rep['seconds']:.1f} s; solves/s = 1 / (s per outer iteration x "
+              f"{REF_OUTER_ITERATIONS} outer iterations per solve)")
+    return {"metric": METRIC, "value": rate, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_iter,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD["name"], "sample": f"{nx}^3"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"oracle full solves at {nx}^3 ({r['n']} vertices, "
-                                       f"{work} outer+inner iterations), scaled by vertices and by "
-                                       f"iterations extrapolated as (side)^{expo:.2f} from "
-                                       f"{nx * 2 // 3}^3 and {nx}^3 to {work_full:.0f}"},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD["name"] if args.nx == 128 else f"grid3d_{args.nx}^3",
+                       "step": (f"one outer PCG iteration of the oracle ({WORKLOAD['inner_maxit']} inner "
+                                f"iterations); the timed region holds the {rep['outer']} that fit "
+                                f"{cap:.0f} s"),
+                       "host": hd},
+            "cpu_baseline": {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():

@@ -365,7 +365,11 @@ lap_status lap_pcg_solve_host(lap_handle h, const double *h_b, double *h_x, void
  * else LAP_ERR_UNSUPPORTED.  Every (graph, column)
  * pair runs its own CG with its own scalars and stops on its own; the
  * matvecs and sweeps of all pairs are batched.  infos (optional) receives
- * sum(nrhs) entries in (graph, column) order.
+ * sum(nrhs) entries in (graph, column) order.  Two or more graphs whose
+ * handles share the solve settings (precision, mu, tol, maxit, check_every,
+ * refinement) and have at most 256 right-hand sides each are merged into a
+ * temporary solve group (lap_group_create below: one launch per PCG phase
+ * for all graphs); otherwise the graphs are solved one after another.
  */
 lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, const int32_t *nrhs,
                                  const double *const *d_B, double *const *d_X, void *stream,

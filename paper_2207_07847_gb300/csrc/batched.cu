@@ -1,4 +1,7 @@
 // Batched solves: many right-hand sides per graph, each with its own CG.
+// Several graphs with the same solve settings go to a merged solve group
+// (group.cu: one launch per phase for all graphs); otherwise, and for one
+// graph, the following.
 //
 // One graph's columns are solved together: every matvec is an SpMM over the
 // block vector, every sweep of the sparsifier solve handles all columns, and
@@ -166,6 +169,26 @@ extern "C" lap_status lap_pcg_solve_batched(int32_t ng, const lap_handle *hs, co
         if (hs[g]->m.opt.prec == LAP_PREC_MSP && hs[g]->m.levels < 2) return LAP_ERR_UNSUPPORTED;
     }
     cudaStream_t user = static_cast<cudaStream_t>(stream);
+    // several graphs with the same solve settings: one merged group, one
+    // launch per PCG phase for all of them (group.cu)
+    if (ng >= 2) {
+        bool same = true;
+        for (int g = 0; g < ng && same; ++g) {
+            const lap_handle_s &h = *hs[g], &h0 = *hs[0];
+            const lap_options &a = h.m.opt, &b = h0.m.opt;
+            same = nrhs[g] <= 256 && h.m.levels >= 2 && a.prec == b.prec && a.precision == b.precision &&
+                   h.m.mu == h0.m.mu && h.device == h0.device && a.tol == b.tol && a.maxit == b.maxit &&
+                   a.check_every == b.check_every && a.max_refine == b.max_refine &&
+                   a.refine_tol == b.refine_tol;
+        }
+        if (same) {
+            lap_group grp = nullptr;
+            lap_status st = lap_group_create(ng, hs, &grp);
+            if (st == LAP_OK) st = lap_pcg_solve_group(grp, nrhs, d_B, d_X, stream, infos);
+            lap_group_destroy(grp);
+            return st;
+        }
+    }
     lap_status result = LAP_OK;
     size_t off = 0;
     std::vector<lap_solve_info> scratch;

@@ -71,8 +71,9 @@ def test_reference_arm_prints_the_contract_line():
     env = dict(os.environ)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
+    # a small instance of the workload's generator and a short timed region
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0"],
+                          "--steps", "1", "--warmup", "0", "--nx", "14", "--oracle-cap-s", "1"],
                          capture_output=True, text=True, env=env, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
@@ -85,6 +86,7 @@ def test_reference_arm_prints_the_contract_line():
     assert r["value"] > 0 and r["higher_is_better"] is True
     cb = r["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
+    assert r["config"]["host"]["nproc"] >= 1 and r["config"]["host"]["cpu_model"]
     e = r["e2e"]
     assert e["value"] == r["value"] and e["unit"] == r["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

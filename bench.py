@@ -41,7 +41,7 @@ FP64_ALU_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (no measured figu
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current
 # kernel, scaled to the 128^3 workload (profiles/k_sell_f32_LH_grid3d96.md);
 # removed whenever the kernel changes.
-MEASURED_TRAFFIC = {"spmv_LH": 1.843e9}
+MEASURED_TRAFFIC = {"spmv_LH": 1.803e9}
 
 
 def parse():
@@ -82,6 +82,9 @@ def parse():
                     help="seconds of timed oracle iterations per oracle leg")
     ap.add_argument("--sweep-inner", action="store_true",
                     help="only sweep the PEGP inner cap and tolerance at the workload")
+    ap.add_argument("--kernel-only", default=None,
+                    help="profiling: set up the workload at --nx and time one lap_kernel_bench kernel "
+                         "(FP32, one warm-up and --steps launches) inside the NVTX range 'kernel'")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -386,7 +389,8 @@ def bench_ours(args, rank, world):
 
     # the oracle legs: their setups run on other host cores while the GPU is measured
     oracle_procs, samples = [], None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile and not args.sweep_inner:
+    if (rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile and not args.sweep_inner
+            and not args.kernel_only):
         try:
             oracle_procs = [(t, start_oracle(args.nx, args.prec, args.oracle_cap_s, t, True))
                             for t in (1, os.cpu_count() or 1)]
@@ -398,6 +402,18 @@ def bench_ours(args, rank, world):
                   seed=WORKLOAD["wseed"])
     if args.sweep_inner:
         return sweep_inner(args, g, dev)
+    if args.kernel_only:
+        hk = P.lap_setup(g, prec=args.prec, mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                         tol=WORKLOAD["tol"], inner_tol=WORKLOAD["inner_tol"],
+                         inner_maxit=WORKLOAD["inner_maxit"])
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("kernel")
+        ms, by = P.lap_kernel_bench(hk, args.kernel_only, 1, args.steps)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        hk.close()
+        print(f"[bench] {args.kernel_only} at {args.nx}^3: {ms * 1e3:.1f} us, {by / 1e9:.4f} GB", file=sys.stderr)
+        return None
     t0 = time.perf_counter()
     h = P.lap_setup(g, prec=args.prec, mu=WORKLOAD["mu"], precision="mixed",
                     seed=WORKLOAD["setup_seed"], tol=WORKLOAD["tol"],

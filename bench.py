@@ -82,6 +82,9 @@ def parse():
                     help="seconds of timed oracle iterations per oracle leg")
     ap.add_argument("--sweep-inner", action="store_true",
                     help="only sweep the PEGP inner cap and tolerance at the workload")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="profiling: one batched solve of the R-MAT workload (--batched-scale, "
+                         "--batched-rhs) capped at this many iterations, inside the NVTX range 'batched'")
     ap.add_argument("--kernel-only", default=None,
                     help="profiling: set up the workload at --nx and time one lap_kernel_bench kernel "
                          "(FP32, one warm-up and --steps launches) inside the NVTX range 'kernel'")
@@ -390,7 +393,7 @@ def bench_ours(args, rank, world):
     # the oracle legs: their setups run on other host cores while the GPU is measured
     oracle_procs, samples = [], None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile and not args.sweep_inner
-            and not args.kernel_only):
+            and not args.kernel_only and not args.profile_batched):
         try:
             oracle_procs = [(t, start_oracle(args.nx, args.prec, args.oracle_cap_s, t, True))
                             for t in (1, os.cpu_count() or 1)]
@@ -400,6 +403,22 @@ def bench_ours(args, rank, world):
             print(f"[bench] oracle legs not started: {e}", file=sys.stderr)
     g = gg.grid3d(args.nx, weights="loguniform", lo=WORKLOAD["wlo"], hi=WORKLOAD["whi"],
                   seed=WORKLOAD["wseed"])
+    if args.profile_batched:
+        gb = gg.rmat(args.batched_scale, 16, seed=5)
+        hb = P.lap_setup(gb, prec="msp", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                         tol=WORKLOAD["tol"], maxit=args.profile_batched)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(500)
+        B = torch.randn(args.batched_rhs, gb.n, dtype=torch.float64, device=dev, generator=gen)
+        X = torch.empty_like(B)
+        P.lap_pcg_solve_batched([hb], [B], [X])                 # warm-up (autotune, graphs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("batched")
+        P.lap_pcg_solve_batched([hb], [B], [X])
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        hb.close()
+        return None
     if args.sweep_inner:
         return sweep_inner(args, g, dev)
     if args.kernel_only:

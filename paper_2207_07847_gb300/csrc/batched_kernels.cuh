@@ -169,24 +169,56 @@ kb_long_chunks(int nchunks, int R, int CT, const int *__restrict__ chunk_row,
                const int *__restrict__ lci, const V *__restrict__ lw, const V *__restrict__ x,
                V *__restrict__ chunk_part)
 {
+    // entries outermost: each entry's index and weight are loaded once and
+    // the R / CT column tiles of its neighbour's row read one after another
+    // (every column still sums its entries in the same order)
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
+    const int nj = R / CT;
+    __shared__ V red[kBThreads];
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int row = lrow[chunk_row[ch]];
-        for (int j = 0; j < R / CT; ++j) {
-            const int c = cl + j * CT;
-            const V xi = x[(size_t)row * R + c];
-            V s = V(0);
-            for (int64_t p = chunk_beg[ch] + o; p < chunk_beg[ch + 1]; p += S)
-                s += lw[p] * (xi - x[(size_t)lci[p] * R + c]);
-            // reduce over the S row groups
-            __shared__ V red[kBThreads];
-            red[threadIdx.x] = s;
+        V xi[8], sj[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            xi[j] = j < nj ? x[(size_t)row * R + cl + j * CT] : V(0);
+            sj[j] = V(0);
+        }
+        const int64_t pe = chunk_beg[ch + 1];
+        int64_t p = chunk_beg[ch] + o;
+        for (; p + S < pe; p += 2 * S) {          // two entries in flight
+            const V w0 = lw[p], w1 = lw[p + S];
+            const V *x0 = x + (size_t)lci[p] * R + cl;
+            const V *x1 = x + (size_t)lci[p + S] * R + cl;
+            V a0[8], a1[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nj) {
+                    a0[j] = x0[j * CT];
+                    a1[j] = x1[j * CT];
+                }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nj) {
+                    sj[j] += w0 * (xi[j] - a0[j]);
+                    sj[j] += w1 * (xi[j] - a1[j]);
+                }
+        }
+        if (p < pe) {
+            const V wv = lw[p];
+            const V *xr = x + (size_t)lci[p] * R + cl;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nj) sj[j] += wv * (xi[j] - xr[j * CT]);
+        }
+        // reduce over the S row groups, one column tile at a time
+        for (int j = 0; j < nj; ++j) {
+            red[threadIdx.x] = sj[j];
             __syncthreads();
             for (int st = S / 2; st > 0; st >>= 1) {
                 if (o < st) red[threadIdx.x] += red[threadIdx.x + st * CT];
                 __syncthreads();
             }
-            if (o == 0) chunk_part[(size_t)ch * R + c] = red[threadIdx.x];
+            if (o == 0) chunk_part[(size_t)ch * R + cl + j * CT] = red[threadIdx.x];
             __syncthreads();
         }
     }
@@ -205,20 +237,40 @@ kb_spmm(int n, int R, int CT, const int *__restrict__ rp, const int *__restrict_
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
     double acc[2][8];
     for (int j = 0; j < 8; ++j) acc[0][j] = acc[1][j] = 0.0;
+    const int nj = R / CT;
     for (int i = blockIdx.x * S + o; i < n; i += gridDim.x * S) {
         const bool lng = is_long && is_long[i];
         const int b = rp[i], e = rp[i + 1];
-        for (int j = 0; j < R / CT; ++j) {
+        // the row's entries outermost (index and weight loaded once, the
+        // neighbour's column tiles read in turn); per column the same order
+        V xv[8], sv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            xv[j] = j < nj ? x[(size_t)i * R + cl + j * CT] : V(0);
+            sv[j] = V(0);
+        }
+        if (lng) {
+            const int li = lrow_of[i];
+            for (int ch = lchunk_ptr[li]; ch < lchunk_ptr[li + 1]; ++ch)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < nj) sv[j] += chunk_part[(size_t)ch * R + cl + j * CT];
+        } else {
+            for (int p = b; p < e; ++p) {
+                const V wv = w[p];
+                const V *xr = x + (size_t)ci[p] * R + cl;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < nj) sv[j] += wv * (xv[j] - xr[j * CT]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= nj) break;
             const int c = cl + j * CT;
             const size_t k = (size_t)i * R + c;
-            const V xi = x[k];
-            V s = V(0);
-            if (lng) {
-                const int li = lrow_of[i];
-                for (int ch = lchunk_ptr[li]; ch < lchunk_ptr[li + 1]; ++ch) s += chunk_part[(size_t)ch * R + c];
-            } else {
-                for (int p = b; p < e; ++p) s += w[p] * (xi - x[(size_t)ci[p] * R + c]);
-            }
+            const V xi = xv[j];
+            const V s = sv[j];
             if (MODE == 1 || MODE == 3) {
                 const double rv = Bs[k] - (double)s;
                 if (MODE == 1 || yres) yres[k] = rv;

@@ -920,13 +920,24 @@ def bench_handshake(args, dev, world):
     stream = torch.cuda.current_stream()
     x = torch.empty(g.n, dtype=torch.float64, device=dev)
     bs = [torch.as_tensor(gg.rhs(g.n, seed=950 + i), device=dev) for i in range(2)]
-    out = {"workload": f"grid3d_{args.nx}^3_loguniform, matching = handshake"}
+    out = {"workload": f"grid3d_{args.nx}^3_loguniform, matching = handshake",
+           "setup": "setup_s: lap_setup with the hierarchy and L_H built on the host threads; "
+                    "setup_device_s: the same setup with them built by device kernels "
+                    "(setup_device = 1, bit-exact with the host build); the solves use the latter"}
     for prec in ("msp", "pegp_inner"):
+        kw = dict(prec=prec, mu=WORKLOAD["mu"], precision="mixed", matching="handshake",
+                  tol=WORKLOAD["tol"], inner_tol=WORKLOAD["inner_tol"],
+                  inner_maxit=WORKLOAD["inner_maxit"], maxit=30000, timeout_s=120.0)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = P.lap_setup(g, prec=prec, mu=WORKLOAD["mu"], precision="mixed", matching="handshake",
-                        tol=WORKLOAD["tol"], inner_tol=WORKLOAD["inner_tol"],
-                        inner_maxit=WORKLOAD["inner_maxit"], maxit=30000, timeout_s=120.0)
+        h = P.lap_setup(g, **kw)
+        torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
+        h.close()
+        t0 = time.perf_counter()
+        h = P.lap_setup(g, setup_device=1, **kw)
+        torch.cuda.synchronize()
+        setup_device_s = time.perf_counter() - t0
         P.lap_pcg_solve(h, bs[0], x)                              # warm-up
         ranks_barrier(world)
         torch.cuda.synchronize()
@@ -938,6 +949,7 @@ def bench_handshake(args, dev, world):
         ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         out[prec] = {"value": whole_job_rate(1, world, ms), "unit": "solves/s",
                      "levels": P.lap_get_hierarchy_info(h)["levels"], "setup_s": round(setup_s, 2),
+                     "setup_device_s": round(setup_device_s, 2),
                      "iterations": info.iterations, "inner_iterations": info.inner_iterations,
                      "relres": info.relres, "status": info.status}
         h.close()

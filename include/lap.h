@@ -129,7 +129,13 @@ typedef struct lap_options {
     int32_t restart;       /* FGMRES cycle length m, 1..128 (default 30)          */
     int32_t matching;      /* lap_matching: the coarsening's matching pass
                               (default LAP_MATCH_GREEDY, the paper's)           */
-    int32_t reserved[2];
+    int32_t setup_device;  /* 1: the hierarchy (matching, coarse graphs, degrees,
+                              out-weights) and PEGP's L_H are built by device
+                              kernels on the setup stream, bit-exact with the
+                              host build; needs matching = LAP_MATCH_HANDSHAKE
+                              (else LAP_ERR_INVALID_ARG); ignored with host_only.
+                              Default 0: host threads                           */
+    int32_t reserved[1];
 } lap_options;
 
 typedef struct lap_solve_info {

@@ -47,7 +47,7 @@ class lap_options(C.Structure):
                 ("check_every", C.c_int32), ("timeout_s", C.c_double),
                 ("spmv_tpr", C.c_int32), ("host_only", C.c_int32),
                 ("stall_window", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
-                ("matching", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("matching", C.c_int32), ("setup_device", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class lap_solve_info(C.Structure):

@@ -20,8 +20,8 @@ OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "liblap.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "spectrum.cpp", "driver.cu", "solve.cu", "batched.cu", "group.cu", "serve.cu",
-           "noalloc.cu"]
+SOURCES = ["setup.cpp", "setup_device.cu", "spectrum.cpp", "driver.cu", "solve.cu", "batched.cu", "group.cu",
+           "serve.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -109,8 +109,16 @@ struct HostModel {
 
 lap_status validate_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
                         std::string *why);
+// The host model of one graph: hierarchy, tree order, sparsifier data and
+// (PEGP) L_H.  With opt.setup_device (and a GPU) the hierarchy and L_H come
+// from device kernels on `stream` (setup_device.cu), bit-exact with the host's.
 lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
-                       const lap_options &opt, HostModel &m);
+                       const lap_options &opt, HostModel &m, void *stream = nullptr);
+// The parts of build_model (m.opt and m.mu set first).
+void build_hierarchy_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *w, HostModel &m);
+lap_status finish_model(HostModel &m);
+lap_status device_build_model(int64_t n, const int64_t *rp, const int32_t *ci, const double *w, HostModel &m,
+                              void *stream);
 // edges of H (which = 0) or T (which = 1) in the hierarchy's expanded numbering, i < j
 void expanded_edges(const HostModel &m, int which, std::vector<int64_t> &I,
                     std::vector<int64_t> &J, std::vector<double> &W);

@@ -578,13 +578,29 @@ void build_pegp(HostModel &m)
 
 // ---------------------------------------------------------------------------
 lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
-                       const lap_options &opt, HostModel &m)
+                       const lap_options &opt, HostModel &m, void *stream)
 {
     m.opt = opt;
     m.mu = opt.mu > 0.0 ? opt.mu : 1.0 / std::sqrt(static_cast<double>(n));
     if (!(m.mu > 0.0 && m.mu < 1.0)) return LAP_ERR_INVALID_ARG;
     if (opt.coarse_max < 1 || opt.max_levels < 0) return LAP_ERR_INVALID_ARG;
+    if (opt.setup_device && !opt.host_only) {
+        // hierarchy and L_H assembled by device kernels (handshake matching only)
+        if (opt.matching != LAP_MATCH_HANDSHAKE) return LAP_ERR_INVALID_ARG;
+        return device_build_model(n, rp, ci, w, m, stream);
+    }
+    build_hierarchy_host(n, rp, ci, w, m);
+    const lap_status st = finish_model(m);
+    if (st != LAP_OK) return st;
+    if (opt.prec == LAP_PREC_PEGP_INNER || opt.prec == LAP_PREC_PEGP_EXACT) build_pegp(m);
+    return LAP_OK;
+}
 
+// Aggregation hierarchy on the host: levels, aggregates, pairs, degrees and
+// out-weights (the fields a device builder fills the same way).
+void build_hierarchy_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *w, HostModel &m)
+{
+    const lap_options &opt = m.opt;
     m.lev.clear();
     m.lev.emplace_back();
     {
@@ -622,6 +638,13 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
         }
         m.lev.push_back(std::move(C));
     }
+}
+
+// Everything after the hierarchy but L_H: tree order, the sparsifier's
+// elimination data, the level-1 Laplacian in tree order, the dense top-level
+// pseudo-inverse and T's edge count.
+lap_status finish_model(HostModel &m)
+{
     const int l = static_cast<int>(m.lev.size());
     m.levels = l;
     m.offset.assign(static_cast<size_t>(l) + 1, 0);
@@ -759,8 +782,6 @@ lap_status build_model(int64_t n, const int64_t *rp, const int32_t *ci, const do
         e += m.lev[l - 1].rp[m.lev[l - 1].n] / 2;                  // top level
         m.edges_T = e;
     }
-
-    if (opt.prec == LAP_PREC_PEGP_INNER || opt.prec == LAP_PREC_PEGP_EXACT) build_pegp(m);
     return LAP_OK;
 }
 

@@ -140,13 +140,14 @@ lap_status lap_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     if (o.krylov != LAP_KRYLOV_CG && o.krylov != LAP_KRYLOV_FGMRES) return LAP_ERR_INVALID_ARG;
     if (o.restart < 1 || o.restart > 128) return LAP_ERR_INVALID_ARG;
     if (o.matching != LAP_MATCH_GREEDY && o.matching != LAP_MATCH_HANDSHAKE) return LAP_ERR_INVALID_ARG;
+    if (o.setup_device != 0 && o.setup_device != 1) return LAP_ERR_INVALID_ARG;
     std::string why;
     lap_status st = validate_csr(n, row_ptr, col_idx, w, &why);
     if (st != LAP_OK) return st;
     std::unique_ptr<lap_handle_s> h(new (std::nothrow) lap_handle_s());
     if (!h) return LAP_ERR_OOM;
     try {
-        st = build_model(n, row_ptr, col_idx, w, o, h->m);
+        st = build_model(n, row_ptr, col_idx, w, o, h->m, stream);
     } catch (const std::bad_alloc &) {
         return LAP_ERR_OOM;
     }

@@ -259,3 +259,17 @@ def test_host_only_handle_refuses_device_work():
     g = gg.grid2d(8)
     h = P.lap_setup(g, host_only=1)
     assert P.lib().lap_pcg_solve(h, 8, 16, None, None) == 1
+
+
+def test_device_setup_option_validation():
+    """setup_device needs the handshake matching; host_only ignores it (the
+    host build runs); other values are rejected."""
+    g = gg.grid2d(12)
+    assert P.lap_setup_status(g.row_ptr, g.col_idx, g.w, setup_device=1, matching="greedy") == 1
+    assert P.lap_setup_status(g.row_ptr, g.col_idx, g.w, setup_device=2, matching="handshake",
+                              host_only=1) == 1
+    h = P.lap_setup(g, setup_device=1, matching="handshake", host_only=1, prec="pegp_inner")
+    ref = P.lap_setup(g, matching="handshake", host_only=1, prec="pegp_inner")
+    for which in (0, 1):
+        for a, b in zip(P.lap_get_expanded_edges(h, which), P.lap_get_expanded_edges(ref, which)):
+            assert np.array_equal(a, b)

@@ -315,7 +315,9 @@ lap_status retire_t(lap_server_s &S, GraphBatch &gb)
     const auto now = Clock::now();
     for (int c = 0; c < R; ++c) {
         Request *r = gb.owner[c];
-        if (!r || c != r->c0) continue;
+        // a request admitted after this chunk was launched has not started:
+        // its columns still hold the stopped states of their previous owner
+        if (!r || c != r->c0 || !r->started) continue;
         bool stopped = true;
         for (int j = r->c0; j < r->c0 + r->nrhs; ++j) stopped &= gb.cols[j].flag != kRun;
         bool cancel;

@@ -520,6 +520,12 @@ def bench_ours(args, rank, world):
     if args.prec == "pegp_inner":
         m_, b_ = P.lap_kernel_bench(h, "spmv_LH", 0, 10)
         other["spmv_LH_f64"] = {"us": round(m_ * 1e3, 2), "GB/s": round(b_ / (m_ * 1e-3) / 1e9, 1)}
+        # the stored-diagonal form of the same matvec (timed only; the solves
+        # use the edge-difference form): one multiply-add per entry in place of
+        # a subtraction and a multiply-add, one more vector read
+        for pname, pid in (("f64", 0), ("f32", 1)):
+            m_, b_ = P.lap_kernel_bench(h, "spmv_LH_diag", pid, 10)
+            other[f"spmv_LH_diag_{pname}"] = {"us": round(m_ * 1e3, 2), "GB/s": round(b_ / (m_ * 1e-3) / 1e9, 1)}
 
     failed = [i.as_dict() for i in inf_mixed + inf_fp64 + inf_e2e if i.status != 0]
     # the paper's sparsifier alone (MSP) on the same system, for comparison
@@ -620,6 +626,7 @@ def bench_powerlaw(args, dev, world):
     """Chung-Lu power-law graph (2^20 vertices, mean degree 16, exponent 2.5,
     largest component, weights uniform in (0, 1]): PCG with the MSP, mixed
     precision against plain FP64, one N(0,1) right-hand side per solve."""
+    import numpy as np
     import torch
 
     import graphgen as gg
@@ -635,6 +642,17 @@ def bench_powerlaw(args, dev, world):
     x = torch.empty(g.n, dtype=torch.float64, device=dev)
     out = {"workload": f"chunglu_{args.powerlaw_n}_d16_g2.5_uniform01_MSP_mu0.8", "n": g.n,
            "nnz": P.lap_get_hierarchy_info(h)["nnz"], "gen_s": round(gen_s, 2), "setup_s": round(setup_s, 2)}
+    # the matvec on hub rows: SELL slices plus chunked long rows, against the copy bandwidth
+    deg = np.diff(np.asarray(g.row_ptr))
+    peak, peak_kind = measured_peaks()
+    spmv = {"max_degree": int(deg.max()), "mean_degree": round(float(deg.mean()), 2),
+            "entries_in_rows_over_8x_mean": round(float(deg[deg > 8 * deg.mean()].sum() / deg.sum()), 4)}
+    for prec_name, prec_id in (("fp32", 1), ("fp64", 0)):
+        ms_, by_ = P.lap_kernel_bench(h, "spmv_L", prec_id, 20)
+        spmv[prec_name] = {"us_per_launch": round(ms_ * 1e3, 2), "bytes_per_launch": by_,
+                           "gbs": round(by_ / (ms_ * 1e-3) / 1e9, 1),
+                           "frac": round(by_ / (ms_ * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind}
+    out["spmv_L"] = spmv
     for precision in ("mixed", "fp64", "fgmres"):
         # "fgmres": the paper's outer method, flexible GMRES(30), FP64
         if precision == "fgmres":

@@ -228,6 +228,10 @@ lap_status lap_update_options(lap_handle h, const lap_options *opts);
  *             expanded-space MSP sweep, reductions, new direction;
  *             LAP_PREC_PEGP_INNER)
  *   kernel 8: the expanded-space MSP solve y~ = L_T^+ f alone (PEGP inner)
+ *   kernel 9: kernel 1 in the stored-diagonal form y = diag(L_H) x - W x
+ *             (one multiply-add per entry instead of a subtraction and a
+ *             multiply-add, the diagonal read too; the solves use kernel 1's
+ *             edge-difference form)
  * in FP64 (precision 0) or FP32 (precision 1, LAP_MIXED handles).  Runs `reps`
  * back-to-back launches (sequences for kernels 2, 7, 8) on the handle's
  * stream timed by CUDA events and writes the mean milliseconds per launch and

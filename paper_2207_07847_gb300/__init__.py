@@ -271,7 +271,8 @@ def lap_update_options(h: Handle, **opts):
 
 
 KERNELS = {"spmv_L": 0, "spmv_LH": 1, "msp_sweep": 2, "update_up1": 3, "msp_tail": 4,
-           "band_down1": 5, "pegp_gemv": 6, "inner_iteration": 7, "msp_tilde": 8}
+           "band_down1": 5, "pegp_gemv": 6, "inner_iteration": 7, "msp_tilde": 8,
+           "spmv_LH_diag": 9}
 
 
 def lap_kernel_bench(h: Handle, kernel, precision=0, reps=20):

@@ -185,25 +185,26 @@ kb_long_chunks(int nchunks, int R, int CT, const int *__restrict__ chunk_row,
         }
         const int64_t pe = chunk_beg[ch + 1];
         int64_t p = chunk_beg[ch] + o;
-        for (; p + S < pe; p += 2 * S) {          // two entries in flight
-            const V w0 = lw[p], w1 = lw[p + S];
-            const V *x0 = x + (size_t)lci[p] * R + cl;
-            const V *x1 = x + (size_t)lci[p + S] * R + cl;
-            V a0[8], a1[8];
+        // U entries in flight (their neighbour rows loaded before any is
+        // added), then added in entry order
+        constexpr int U = sizeof(V) == 4 ? 4 : 2;
+        for (; p + (U - 1) * S < pe; p += U * S) {
+            V wu[U], a[U][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j < nj) {
-                    a0[j] = x0[j * CT];
-                    a1[j] = x1[j * CT];
-                }
+            for (int u = 0; u < U; ++u) {
+                wu[u] = lw[p + u * S];
+                const V *xu = x + (size_t)lci[p + u * S] * R + cl;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j < nj) {
-                    sj[j] += w0 * (xi[j] - a0[j]);
-                    sj[j] += w1 * (xi[j] - a1[j]);
-                }
+                for (int j = 0; j < 8; ++j)
+                    if (j < nj) a[u][j] = xu[j * CT];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < nj) sj[j] += wu[u] * (xi[j] - a[u][j]);
         }
-        if (p < pe) {
+        for (; p < pe; p += S) {
             const V wv = lw[p];
             const V *xr = x + (size_t)lci[p] * R + cl;
 #pragma unroll

@@ -517,6 +517,41 @@ void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
 // --------------------------------------------------------------------------
 // kernel sequences
 // --------------------------------------------------------------------------
+// The SELL matvec of A in the stored-diagonal form (y = dg x - W x, see
+// k_sell), with A's tuned grid, lane groups and load policy; timed by
+// lap_kernel_bench against the edge-difference form the solves use.
+template <typename V>
+void spmv_diag(const lap_handle_s &h, const DevCsr<V> &A, const V *dg, const V *x, V *y, const CgState &st,
+               cudaStream_t s)
+{
+    const bool hint = A.stream_hint != 0;
+    if (A.nchunks > 0) {
+        const int gc = grid_for(h, static_cast<int64_t>(A.nchunks) * 32);
+        if (hint)
+            k_long_chunks<V, true, true><<<gc, kBlock, 0, s>>>(A.nchunks, A.chunk_row, A.chunk_beg, A.lrow, A.lci,
+                                                               A.lw, x, A.chunk_part, st.sc, 0);
+        else
+            k_long_chunks<V, false, true><<<gc, kBlock, 0, s>>>(A.nchunks, A.chunk_row, A.chunk_beg, A.lrow, A.lci,
+                                                                A.lw, x, A.chunk_part, st.sc, 0);
+    }
+    const int g = A.sell_grid > 0 ? A.sell_grid : grid_for(h, static_cast<int64_t>(A.nslices + A.nlong) * 32);
+#define LAP_SELL_D(VEC, HINT)                                                                              \
+    k_sell<V, 2, VEC, HINT, true><<<g, kBlock, 0, s>>>(A.n, A.nslices, A.sptr, A.lmask, A.rowperm, A.eci,  \
+                                                       A.ew, A.nlong, A.lrow, A.lchunk_ptr, A.chunk_part, \
+                                                       x, y, nullptr, nullptr, st.sc, st.part, st.ticket, dg)
+    if (A.vec == 4) {
+        if (hint) LAP_SELL_D(4, true);
+        else LAP_SELL_D(4, false);
+    } else if (A.vec == 2) {
+        if (hint) LAP_SELL_D(2, true);
+        else LAP_SELL_D(2, false);
+    } else {
+        if (hint) LAP_SELL_D(1, true);
+        else LAP_SELL_D(1, false);
+    }
+#undef LAP_SELL_D
+}
+
 template <typename V, int MODE>
 void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, const double *bs,
           double *yres, const CgState &st, cudaStream_t s)
@@ -1927,11 +1962,26 @@ double inner_iteration_bytes(const DevCsr<V> &H, const DevMsp<V> &M)
 lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, double *ms, double *bytes)
 {
     if (precision == 1 && !h.L32.w) return LAP_ERR_INVALID_ARG;
-    if ((kernel == 1 || kernel == 7 || kernel == 8) && !h.H64.w) return LAP_ERR_INVALID_ARG;
+    if ((kernel == 1 || kernel == 7 || kernel == 8 || kernel == 9) && !h.H64.w) return LAP_ERR_INVALID_ARG;
     if ((kernel == 7 || kernel == 8) && (h.M64.levels < 2 || !is_pegp(h))) return LAP_ERR_INVALID_ARG;
     if (kernel == 6 && !h.G64) return LAP_ERR_INVALID_ARG;
-    if (kernel < 0 || kernel > 8) return LAP_ERR_INVALID_ARG;
+    if (kernel == 9 && static_cast<int64_t>(h.m.LH.diag.size()) != h.H64.n) return LAP_ERR_INVALID_ARG;
+    if (kernel < 0 || kernel > 9) return LAP_ERR_INVALID_ARG;
     const cudaStream_t s = h.s;
+    // kernel 9: L_H's diagonal on the device in the timed precision
+    DevBuf dgbuf;
+    if (kernel == 9) {
+        const int64_t nt = h.H64.n;
+        if (!dgbuf.alloc(static_cast<size_t>(nt) * (precision == 1 ? 4 : 8))) return LAP_ERR_OOM;
+        if (precision == 1) {
+            std::vector<float> d32(h.m.LH.diag.begin(), h.m.LH.diag.end());
+            LAP_CK(cudaMemcpyAsync(dgbuf.p, d32.data(), 4 * nt, cudaMemcpyHostToDevice, s));
+            LAP_CK(cudaStreamSynchronize(s));
+        } else {
+            LAP_CK(cudaMemcpyAsync(dgbuf.p, h.m.LH.diag.data(), 8 * nt, cudaMemcpyHostToDevice, s));
+            LAP_CK(cudaStreamSynchronize(s));
+        }
+    }
     cudaEvent_t e0, e1;
     LAP_CK(cudaEventCreate(&e0));
     LAP_CK(cudaEventCreate(&e1));
@@ -1970,6 +2020,7 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
             }
             case 7: inner_iteration<V>(h, Sel<V>::H(h), M, Sel<V>::e(h), h.stb, s); break;
             case 8: msp_tilde<V>(h, M, Sel<V>::e(h).A, Sel<V>::e(h).Y, h.stb.sc, s); break;
+            case 9: spmv_diag<V>(h, Sel<V>::H(h), dgbuf.as<V>(), Sel<V>::e(h).p, Sel<V>::e(h).q, h.stb, s); break;
             default: {
                 const BandParams<V> &P = M.band_n[0];
                 k_band_down<V, true, false><<<P.grid_down, kBandThreads, static_cast<size_t>(P.smem), s>>>(
@@ -1982,6 +2033,9 @@ lap_status kernel_bench(lap_handle_s &h, int kernel, int precision, int reps, do
         if (kernel == 0 || kernel == 1) {
             const auto &A = kernel == 0 ? Sel<V>::L(h) : Sel<V>::H(h);
             by = A.nnz * (4.0 + sv) + 4.0 * (A.n + 1) + 2.0 * sv * A.n;
+        } else if (kernel == 9) {
+            const auto &A = Sel<V>::H(h);
+            by = A.nnz * (4.0 + sv) + 4.0 * (A.n + 1) + 3.0 * sv * A.n;   // the diagonal read too
         } else if (kernel == 2) {
             by = sweep_bytes(M);
         } else if (kernel == 3) {

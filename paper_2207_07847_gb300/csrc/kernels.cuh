@@ -257,63 +257,72 @@ __device__ __forceinline__ T ldm(const T *p)
     return __ldg(p);
 }
 
+// One entry of a row sum: w (x_i - x_j) in the edge-difference form, w x_j
+// in the stored-diagonal form (DIAG; the row then finishes as d_i x_i - sum).
+template <bool DIAG, typename V>
+__device__ __forceinline__ V edge_term(V s, V w, V xi, V xj)
+{
+    if (DIAG) return s + w * xj;
+    return s + w * (xi - xj);
+}
+
 // VEC consecutive entries of one lane (a lane group of the SELL layout) with
 // vector loads; the row sum is still accumulated entry by entry.
-template <typename V, int VEC, bool HINT = false> struct LaneGroup;
-template <typename V, bool HINT> struct LaneGroup<V, 1, HINT> {
+template <typename V, int VEC, bool HINT = false, bool DIAG = false> struct LaneGroup;
+template <typename V, bool HINT, bool DIAG> struct LaneGroup<V, 1, HINT, DIAG> {
     __device__ __forceinline__ static V add(V s, V xi, const int *c, const V *w, const V *__restrict__ x)
     {
-        return s + ldm<HINT>(w) * (xi - x[ldm<HINT>(c)]);
+        return edge_term<DIAG>(s, ldm<HINT>(w), xi, x[ldm<HINT>(c)]);
     }
 };
-template <bool HINT> struct LaneGroup<float, 2, HINT> {
+template <bool HINT, bool DIAG> struct LaneGroup<float, 2, HINT, DIAG> {
     __device__ __forceinline__ static float add(float s, float xi, const int *c, const float *w,
                                                 const float *__restrict__ x)
     {
         const int2 cc = ldm<HINT>(reinterpret_cast<const int2 *>(c));
         const float2 ww = ldm<HINT>(reinterpret_cast<const float2 *>(w));
-        s += ww.x * (xi - x[cc.x]);
-        return s + ww.y * (xi - x[cc.y]);
+        s = edge_term<DIAG>(s, ww.x, xi, x[cc.x]);
+        return edge_term<DIAG>(s, ww.y, xi, x[cc.y]);
     }
 };
-template <bool HINT> struct LaneGroup<float, 4, HINT> {
+template <bool HINT, bool DIAG> struct LaneGroup<float, 4, HINT, DIAG> {
     __device__ __forceinline__ static float add(float s, float xi, const int *c, const float *w,
                                                 const float *__restrict__ x)
     {
         const int4 cc = ldm<HINT>(reinterpret_cast<const int4 *>(c));
         const float4 ww = ldm<HINT>(reinterpret_cast<const float4 *>(w));
-        s += ww.x * (xi - x[cc.x]);
-        s += ww.y * (xi - x[cc.y]);
-        s += ww.z * (xi - x[cc.z]);
-        return s + ww.w * (xi - x[cc.w]);
+        s = edge_term<DIAG>(s, ww.x, xi, x[cc.x]);
+        s = edge_term<DIAG>(s, ww.y, xi, x[cc.y]);
+        s = edge_term<DIAG>(s, ww.z, xi, x[cc.z]);
+        return edge_term<DIAG>(s, ww.w, xi, x[cc.w]);
     }
 };
-template <bool HINT> struct LaneGroup<double, 2, HINT> {
+template <bool HINT, bool DIAG> struct LaneGroup<double, 2, HINT, DIAG> {
     __device__ __forceinline__ static double add(double s, double xi, const int *c, const double *w,
                                                  const double *__restrict__ x)
     {
         const int2 cc = ldm<HINT>(reinterpret_cast<const int2 *>(c));
         const double2 ww = ldm<HINT>(reinterpret_cast<const double2 *>(w));
-        s += ww.x * (xi - x[cc.x]);
-        return s + ww.y * (xi - x[cc.y]);
+        s = edge_term<DIAG>(s, ww.x, xi, x[cc.x]);
+        return edge_term<DIAG>(s, ww.y, xi, x[cc.y]);
     }
 };
-template <bool HINT> struct LaneGroup<double, 4, HINT> {
+template <bool HINT, bool DIAG> struct LaneGroup<double, 4, HINT, DIAG> {
     __device__ __forceinline__ static double add(double s, double xi, const int *c, const double *w,
                                                  const double *__restrict__ x)
     {
         const int4 cc = ldm<HINT>(reinterpret_cast<const int4 *>(c));
         const double2 w0 = ldm<HINT>(reinterpret_cast<const double2 *>(w));
         const double2 w1 = ldm<HINT>(reinterpret_cast<const double2 *>(w) + 1);
-        s += w0.x * (xi - x[cc.x]);
-        s += w0.y * (xi - x[cc.y]);
-        s += w1.x * (xi - x[cc.z]);
-        return s + w1.y * (xi - x[cc.w]);
+        s = edge_term<DIAG>(s, w0.x, xi, x[cc.x]);
+        s = edge_term<DIAG>(s, w0.y, xi, x[cc.y]);
+        s = edge_term<DIAG>(s, w1.x, xi, x[cc.z]);
+        return edge_term<DIAG>(s, w1.y, xi, x[cc.w]);
     }
 };
 
 // Partial sums of the long rows, one warp per chunk of <= 4096 entries.
-template <typename V, bool HINT = false>
+template <typename V, bool HINT = false, bool DIAG = false>
 __global__ void __launch_bounds__(kBlock)
 k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__restrict__ chunk_beg,
               const int *__restrict__ lrow, const int *__restrict__ lci, const V *__restrict__ lw,
@@ -329,7 +338,7 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
         // lane l takes entries 128 g + 4 l .. + 3 with one vector load each
 #pragma unroll 2
         for (int64_t p = chunk_beg[c] + 4 * lane; p < chunk_beg[c + 1]; p += 128)
-            s = LaneGroup<V, 4, HINT>::add(s, xi, lci + p, lw + p, x);
+            s = LaneGroup<V, 4, HINT, DIAG>::add(s, xi, lci + p, lw + p, x);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) chunk_part[c] = s;
@@ -340,15 +349,18 @@ k_long_chunks(int nchunks, const int *__restrict__ chunk_row, const int64_t *__r
 // lane l owning the row of slot 32 s + l and reading its entries VEC at a
 // time (see make_sell for the layout); long rows add their chunk partials.
 // The warps stride over the slices; the grid (one or more waves of resident
-// blocks) is chosen per matrix at setup by timing.
-template <typename V, int MODE, int VEC, bool HINT = false>
+// blocks) is chosen per matrix at setup by timing.  DIAG: the stored-diagonal
+// form y_i = dg_i x_i - sum_j w_ij x_j instead (one multiply-add per entry
+// instead of a subtraction and a multiply-add; timed, not used by the solves).
+template <typename V, int MODE, int VEC, bool HINT = false, bool DIAG = false>
 __global__ void __launch_bounds__(kBlock)
 k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__restrict__ lmask,
        const int *__restrict__ rowperm, const int *__restrict__ eci, const V *__restrict__ ew, int nlong,
        const int *__restrict__ lrow,
        const int *__restrict__ lchunk_ptr, const V *__restrict__ chunk_part,
        const V *__restrict__ x, V *__restrict__ y, const double *__restrict__ bs,
-       double *__restrict__ yres, CgScalars *sc, double *part, unsigned *ticket)
+       double *__restrict__ yres, CgScalars *sc, double *part, unsigned *ticket,
+       const V *__restrict__ dg = nullptr)
 {
     if (MODE != 2 && halted(sc)) return;
     const int lane = threadIdx.x & 31;
@@ -386,15 +398,16 @@ k_sell(int n, int nslices, const int64_t *__restrict__ sptr, const unsigned *__r
         const int ng = width / VEC;
 #pragma unroll(VEC == 1 ? 4 : 2)
         for (int g = 0; g < ng; ++g)
-            s = LaneGroup<V, VEC, HINT>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
-        if (valid && !((lmask[task] >> lane) & 1u)) finish(row, xi, s);
+            s = LaneGroup<V, VEC, HINT, DIAG>::add(s, xi, pc + 32 * VEC * g, pw + 32 * VEC * g, x);
+        if (valid && !((lmask[task] >> lane) & 1u)) finish(row, xi, DIAG ? dg[row] * xi - s : s);
     };
     auto long_row = [&](int li) {
         // long row: add its chunk partials in chunk order
         const int row = lrow[li];
         V s = V(0);
         for (int c = lchunk_ptr[li]; c < lchunk_ptr[li + 1]; ++c) s += chunk_part[c];
-        finish(row, x[row], s);
+        const V xi = x[row];
+        finish(row, xi, DIAG ? dg[row] * xi - s : s);
     };
     const int ntask = nslices + nlong;
     for (int task = gwarp; task < ntask; task += nwarp) {          // warp-uniform

@@ -1036,11 +1036,14 @@ def bench_serving(args, dev, world):
     _, t_burst = run_stream(burst, [0.0] * len(burst))
     cap_rhs = float(sum(nr[i] for i in burst)) / t_burst
     lam = args.serve_load * cap_rhs / float(np.mean(nr))     # requests per second
+    print(f"serving: burst of {len(burst)} requests in {t_burst:.1f} s ({cap_rhs:.1f} RHS/s)",
+          file=sys.stderr, flush=True)
     arrivals = np.cumsum(rng.exponential(1.0 / lam, R))
     arrivals -= arrivals[0]
     ranks_barrier(world)
     done, wall = run_stream(list(range(R)), arrivals)
     S.close()
+    print(f"serving: {R} requests in {wall:.1f} s", file=sys.stderr, flush=True)
     lat = [done[i][0] * 1e3 for i in range(R)]
     failed = sum(1 for i in range(R) if done[i][1] != 0)
     failed_info = [dict(done[i][2], graph_n=graphs[gi[i]].n, nrhs=int(nr[i]))

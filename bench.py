@@ -78,6 +78,9 @@ def parse():
                          "closed burst of the first 256 requests")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving line (e.g. 10,000 requests over 64 graphs), printed alone")
+    ap.add_argument("--only", default=None,
+                    choices=["serving", "powerlaw", "batched", "group", "handshake", "pegp_exact"],
+                    help="run this one auxiliary line alone and print it")
     ap.add_argument("--handshake", type=int, default=1,
                     help="1: also solve the headline grid with the deterministic parallel "
                          "matching variant (a method change; reported apart, 0: skip)")
@@ -1146,9 +1149,13 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
     if args.serving_only:
+        args.only = "serving"
+    if args.only:
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
-        res = {"serving": bench_serving(args, dev, world)}
+        line = {"serving": bench_serving, "powerlaw": bench_powerlaw, "batched": bench_batched,
+                "group": bench_group, "handshake": bench_handshake, "pegp_exact": bench_pegp_exact}[args.only]
+        res = {args.only: line(args, dev, world)}
         if rank == 0:
             print(json.dumps(res), flush=True)
         return

@@ -824,8 +824,7 @@ static int64_t choose_long_threshold(const HostCsr &A)
 void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
 {
     const int64_t n = A.n;
-    const bool auto_threshold = long_threshold <= 0;
-    if (auto_threshold) long_threshold = choose_long_threshold(A);
+    if (long_threshold <= 0) long_threshold = choose_long_threshold(A);
     S.n = n;
     S.nslices = (n + 31) / 32;
     S.sptr.assign(static_cast<size_t>(S.nslices) + 1, 0);
@@ -864,60 +863,9 @@ void make_sell(const HostCsr &A, HostSell &S, int64_t long_threshold, int vec)
     });
     // sorting pays only if it saves padding: else keep the rows in place (an
     // empty rowperm: slot = row)
-    bool sorted = slices_size() * 20 < unsorted * 19;
+    const bool sorted = slices_size() * 20 < unsorted * 19;
     if (!sorted)
         for (int64_t r = 0; r < n; ++r) S.rowperm[r] = static_cast<int32_t>(r);
-    // Power-law rows: a window of eight slices still pads to its few longest
-    // rows, and a low threshold sends many medium rows to chunks padded to
-    // 128 entries.  The alternative sorts all short rows by decreasing length
-    // over the whole matrix (slices of near-equal rows, the slice of rank s
-    // padded to the length at rank 32 s) with a threshold of 128, 192 or 256,
-    // and is taken when it stores at most 80% of the entries of the layout
-    // above.  Grid-like matrices keep the layout above (and its locality).
-    if (auto_threshold && n > 0) {
-        auto long_size = [&](int64_t T) {
-            int64_t t = 0;
-            for (int64_t r = 0; r < n; ++r) {
-                const int64_t d = A.rp[r + 1] - A.rp[r];
-                if (d > T) t += (d + 127) / 128 * 128;
-            }
-            return t;
-        };
-        const int64_t current = slices_size() + long_size(long_threshold);
-        int64_t maxd = 0;
-        for (int64_t r = 0; r < n; ++r) maxd = std::max(maxd, A.rp[r + 1] - A.rp[r]);
-        std::vector<int64_t> hist(static_cast<size_t>(maxd) + 1, 0);
-        for (int64_t r = 0; r < n; ++r) ++hist[A.rp[r + 1] - A.rp[r]];
-        auto global_size = [&](int64_t T) {
-            int64_t t = 0, rank = 0;
-            for (int64_t d = std::min(T, maxd); d >= 1; --d) {
-                const int64_t c = hist[d];
-                if (c == 0) continue;
-                const int64_t f = (rank + 31) / 32 * 32;       // first slice start among ranks [rank, rank + c)
-                if (f < rank + c) t += ((rank + c - 1 - f) / 32 + 1) * 32 * d;
-                rank += c;
-            }
-            return t + long_size(T);
-        };
-        int64_t best_t = 0, best = 0;
-        for (int64_t T : {128, 192, 256}) {
-            const int64_t g = global_size(T);
-            if (best_t == 0 || g < best) {
-                best_t = T;
-                best = g;
-            }
-        }
-        if (best * 5 <= current * 4) {
-            long_threshold = best_t;
-            // stable counting sort by decreasing length (long rows count as empty)
-            std::vector<int64_t> start(static_cast<size_t>(maxd) + 2, 0);
-            for (int64_t r = 0; r < n; ++r) ++start[static_cast<size_t>(maxd - len(r)) + 1];
-            for (size_t d = 1; d < start.size(); ++d) start[d] += start[d - 1];
-            for (int64_t r = 0; r < n; ++r)
-                S.rowperm[start[static_cast<size_t>(maxd - len(r))]++] = static_cast<int32_t>(r);
-            sorted = true;
-        }
-    }
     std::vector<int64_t> width(static_cast<size_t>(S.nslices), 0);
     for (int64_t s = 0; s < S.nslices; ++s) {
         for (int64_t lane = 0; lane < 32; ++lane) {

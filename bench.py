@@ -650,11 +650,19 @@ def bench_powerlaw(args, dev, world):
     peak, peak_kind = measured_peaks()
     spmv = {"max_degree": int(deg.max()), "mean_degree": round(float(deg.mean()), 2),
             "entries_in_rows_over_8x_mean": round(float(deg[deg > 8 * deg.mean()].sum() / deg.sum()), 4)}
-    for prec_name, prec_id in (("fp32", 1), ("fp64", 0)):
-        ms_, by_ = P.lap_kernel_bench(h, "spmv_L", prec_id, 20)
-        spmv[prec_name] = {"us_per_launch": round(ms_ * 1e3, 2), "bytes_per_launch": by_,
-                           "gbs": round(by_ / (ms_ * 1e-3) / 1e9, 1),
-                           "frac": round(by_ / (ms_ * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind}
+    # the autotuned choice, then SELL + chunks and the merge-path CSR forced
+    for label, hk in (("tuned", h), ("sell", None), ("merge", None)):
+        if hk is None:
+            hk = P.lap_setup(g, prec="msp", mu=WORKLOAD["mu"], precision="mixed", seed=WORKLOAD["setup_seed"],
+                             spmv_tpr=-1 if label == "sell" else -2)
+        for prec_name, prec_id in (("fp32", 1), ("fp64", 0)):
+            ms_, by_ = P.lap_kernel_bench(hk, "spmv_L", prec_id, 20)
+            spmv[f"{label}_{prec_name}"] = {"us_per_launch": round(ms_ * 1e3, 2), "bytes_per_launch": by_,
+                                            "gbs": round(by_ / (ms_ * 1e-3) / 1e9, 1),
+                                            "frac": round(by_ / (ms_ * 1e-3) / 1e9 / peak, 4),
+                                            "peak_kind": peak_kind}
+        if hk is not h:
+            hk.close()
     out["spmv_L"] = spmv
     for precision in ("mixed", "fp64", "fgmres"):
         # "fgmres": the paper's outer method, flexible GMRES(30), FP64

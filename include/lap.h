@@ -117,7 +117,9 @@ typedef struct lap_options {
     int32_t check_every;   /* outer iterations between host convergence polls (8) */
     double timeout_s;      /* wall-clock limit per solve, <= 0: none (default 0)  */
     int32_t spmv_tpr;      /* matvec kernel: 0 = timed at setup (autotune), -1 =
-                              SELL-32 slices, t > 0 = CSR with t threads per row */
+                              SELL-32 slices, -2 = merge-path CSR (equal shares
+                              of rows and entries per thread), t > 0 = CSR with
+                              t threads per row                                 */
     int32_t host_only;     /* 1: build the host-side setup only and touch no GPU;
                               only the lap_get_* queries work on such a handle  */
     int32_t stall_window;  /* LAP_MIXED: an FP32 inner solve returns to refinement

@@ -41,7 +41,7 @@ struct DevBuf {
 
 // A Laplacian's off-diagonal part on the device, as CSR and as SELL-32 (see
 // HostSell); `kernel` selects the matvec: 0 = SELL, t > 0 = CSR with t threads
-// per row (chosen by timing at setup).
+// per row, kMergeKernel = merge-path CSR (chosen by timing at setup).
 template <typename V> struct DevCsr {
     int n = 0;
     int64_t nnz = 0;
@@ -67,6 +67,12 @@ template <typename V> struct DevCsr {
     int vec = 1;                       // SELL lane-group width (1, 2, 4)
     int sell_grid = 0;                 // SELL blocks per launch (0: one per 8 slices, capped)
     int stream_hint = 0;               // 1: SELL and chunk entries loaded evict-first
+    // merge-path matvec (merge.cuh): per block, the partials of the rows that
+    // run across blocks
+    int merge_nb = 0;
+    int *mg_hrow = nullptr, *mg_trow = nullptr;
+    V *mg_hval = nullptr, *mg_tval = nullptr;
+    unsigned char *mg_hend = nullptr;
 };
 
 template <typename V> struct DevMspLevel {

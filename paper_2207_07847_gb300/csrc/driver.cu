@@ -26,6 +26,7 @@
 #include "fgmres.cuh"
 #include "stretch.cuh"
 #include "kernels.cuh"
+#include "merge.cuh"
 #include "solver.cuh"
 
 namespace lap {
@@ -155,6 +156,14 @@ lap_status upload_csr(lap_handle_s &h, const HostCsr &c, const HostSell &sl, Dev
     d.nchunks = static_cast<int>(sl.chunk_row.size());
     d.chunk_part = dalloc<V>(h, std::max<size_t>(sl.chunk_row.size(), 1));
     if (!d.chunk_part) return LAP_ERR_OOM;
+    d.merge_nb = static_cast<int>((c.n + d.nnz + kMergeTile - 1) / kMergeTile);
+    const size_t nb = static_cast<size_t>(std::max(d.merge_nb, 1));
+    d.mg_hrow = dalloc<int>(h, nb);
+    d.mg_trow = dalloc<int>(h, nb);
+    d.mg_hval = dalloc<V>(h, nb);
+    d.mg_tval = dalloc<V>(h, nb);
+    d.mg_hend = dalloc<unsigned char>(h, nb);
+    if (!d.mg_hrow || !d.mg_trow || !d.mg_hval || !d.mg_tval || !d.mg_hend) return LAP_ERR_OOM;
     return LAP_OK;
 }
 
@@ -487,6 +496,7 @@ void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
         for (int hint = 0; hint < 2; ++hint) cand.push_back({-1, static_cast<int>(std::max<int64_t>(g, 1)), hint});
     }
     for (int t : {2, 4, 8, 16}) cand.push_back({t, 0, 0});
+    cand.push_back({kMergeKernel, 0, 0});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return;
     Cand best = cand[0];
@@ -509,7 +519,7 @@ void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     (void)cudaGetLastError();
-    A.kernel = best.kernel < 0 ? 0 : best.kernel;
+    A.kernel = best.kernel == kMergeKernel ? kMergeKernel : best.kernel < 0 ? 0 : best.kernel;
     A.sell_grid = best.grid;
     A.stream_hint = best.hint;
 }
@@ -556,7 +566,20 @@ template <typename V, int MODE>
 void spmv(const lap_handle_s &h, const DevCsr<V> &A, int tpr, const V *x, V *y, const double *bs,
           double *yres, const CgState &st, cudaStream_t s)
 {
-    if (tpr == 0) tpr = A.kernel;      // 0: the tuned choice, -1: SELL, t > 0: CSR
+    if (tpr == 0) tpr = A.kernel;      // 0: the tuned choice, -1: SELL, -2: merge path, t > 0: CSR
+    if (tpr == kMergeKernel) {
+        CgScalars *sc = st.sc;
+        h.launches += MODE == 2 ? 2 : 3;
+        k_merge<V, MODE><<<A.merge_nb, kBlock, 0, s>>>(A.n, A.nnz, A.rp, A.ci, A.w, x, y, bs, yres, A.mg_hrow,
+                                                        A.mg_hval, A.mg_hend, A.mg_trow, A.mg_tval, sc);
+        k_merge_fix<V, MODE><<<(A.merge_nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+            A.merge_nb, y, bs, yres, A.mg_hrow, A.mg_hval, A.mg_hend, A.mg_trow, A.mg_tval, sc);
+        if (MODE != 2) {
+            const int g = static_cast<int>(std::min<int64_t>((A.n + kBlock - 1) / kBlock, 1024));
+            k_merge_reduce<V, MODE><<<std::max(g, 1), kBlock, 0, s>>>(A.n, x, y, yres, sc, st.part, st.ticket);
+        }
+        return;
+    }
     if (tpr <= 0) {
         const bool hint = A.stream_hint != 0;
         if (A.nchunks > 0) {
@@ -1650,7 +1673,8 @@ lap_status upload_model(lap_handle_s &h, cudaStream_t user)
     h.tpr = 0;
     h.tprH = 0;
     if (m.opt.spmv_tpr != 0) {
-        h.L64.kernel = h.L32.kernel = h.H64.kernel = h.H32.kernel = std::max(m.opt.spmv_tpr, 0);
+        h.L64.kernel = h.L32.kernel = h.H64.kernel = h.H32.kernel =
+            m.opt.spmv_tpr == kMergeKernel ? kMergeKernel : std::max(m.opt.spmv_tpr, 0);
     } else {
         // each copy on its own: the FP64 and FP32 matvecs prefer different shapes
         autotune_spmv<double>(h, h.L64, h.w64.p, h.w64.q);

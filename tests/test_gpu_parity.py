@@ -71,10 +71,11 @@ def case(request):
 
 # --- single operators ---------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", [0, -1, 4])
+@pytest.mark.parametrize("kernel", [0, -1, -2, 4])
 def test_laplacian_apply(case, kernel):
-    """SELL-32 slices (-1), CSR with 4 threads per row (4) and the autotuned
-    choice (0) all equal L x; power-law cases exercise the chunked long rows."""
+    """SELL-32 slices (-1), the merge-path CSR (-2), CSR with 4 threads per row
+    (4) and the autotuned choice (0) all equal L x; power-law cases exercise the
+    chunked long rows and rows split across merge-path threads and blocks."""
     name, g, ho, ops = case
     h = P.lap_setup(g, seed=17, spmv_tpr=kernel)
     x = gg.rhs(g.n, seed=1)

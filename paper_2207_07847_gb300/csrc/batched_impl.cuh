@@ -121,7 +121,7 @@ void bspmm(const lap_handle_s &h, const BatchWork &b, const DevCsr<V> &L, const 
         // its own layout: 32-column tiles, eight row groups splitting the
         // chunk's entries (independent of the SpMM's tuned tile)
         kb_long_chunks<V><<<std::min(L.nchunks, h.grid_cap), kBThreads, 0, s>>>(
-            L.nchunks, R, std::min(R, 32), L.chunk_row, L.chunk_beg, L.lrow, L.lci, L.lw, x, chunk);
+            L.nchunks, R, std::min(R, 32), L.chunk_row, L.chunk_beg, L.lrow, L.lrp, L.rp, L.lci, L.lw, x, chunk);
     }
     h.launches += 1;
     kb_spmm<V, MODE><<<bgrid(h, L.n, R, CT), kBThreads, 0, s>>>(

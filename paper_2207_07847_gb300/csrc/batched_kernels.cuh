@@ -166,6 +166,7 @@ template <typename V>
 __global__ void __launch_bounds__(kBThreads)
 kb_long_chunks(int nchunks, int R, int CT, const int *__restrict__ chunk_row,
                const int64_t *__restrict__ chunk_beg, const int *__restrict__ lrow,
+               const int64_t *__restrict__ lrp, const int *__restrict__ rp,
                const int *__restrict__ lci, const V *__restrict__ lw, const V *__restrict__ x,
                V *__restrict__ chunk_part)
 {
@@ -174,16 +175,20 @@ kb_long_chunks(int nchunks, int R, int CT, const int *__restrict__ chunk_row,
     // (every column still sums its entries in the same order)
     const int S = kBThreads / CT, o = threadIdx.x / CT, cl = threadIdx.x % CT;
     const int nj = R / CT;
-    __shared__ V red[kBThreads];
+    __shared__ V red[8][kBThreads];
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int row = lrow[chunk_row[ch]];
+        const int li = chunk_row[ch];
+        const int row = lrow[li];
         V xi[8], sj[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             xi[j] = j < nj ? x[(size_t)row * R + cl + j * CT] : V(0);
             sj[j] = V(0);
         }
-        const int64_t pe = chunk_beg[ch + 1];
+        // the chunk's real entries: the layout pads each long row to whole
+        // groups of 128 entries (weight 0), which add nothing here
+        const int64_t real_end = lrp[li] + (rp[row + 1] - rp[row]);
+        const int64_t pe = chunk_beg[ch + 1] < real_end ? chunk_beg[ch + 1] : real_end;
         int64_t p = chunk_beg[ch] + o;
         // U entries in flight (their neighbour rows loaded before any is
         // added), then added in entry order
@@ -211,17 +216,23 @@ kb_long_chunks(int nchunks, int R, int CT, const int *__restrict__ chunk_row,
             for (int j = 0; j < 8; ++j)
                 if (j < nj) sj[j] += wv * (xi[j] - xr[j * CT]);
         }
-        // reduce over the S row groups, one column tile at a time
-        for (int j = 0; j < nj; ++j) {
-            red[threadIdx.x] = sj[j];
-            __syncthreads();
-            for (int st = S / 2; st > 0; st >>= 1) {
-                if (o < st) red[threadIdx.x] += red[threadIdx.x + st * CT];
-                __syncthreads();
-            }
-            if (o == 0) chunk_part[(size_t)ch * R + cl + j * CT] = red[threadIdx.x];
+        // reduce over the S row groups, all column tiles at once
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < nj) red[j][threadIdx.x] = sj[j];
+        __syncthreads();
+        for (int st = S / 2; st > 0; st >>= 1) {
+            if (o < st)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < nj) red[j][threadIdx.x] += red[j][threadIdx.x + st * CT];
             __syncthreads();
         }
+        if (o == 0)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nj) chunk_part[(size_t)ch * R + cl + j * CT] = red[j][threadIdx.x];
+        __syncthreads();
     }
 }
 

@@ -495,8 +495,9 @@ void autotune_spmv(lap_handle_s &h, DevCsr<V> &A, V *x, V *y)
         if (waves > 1 && g <= int64_t(h.grid_cap) * (waves - 1)) break;   // no new launch shape
         for (int hint = 0; hint < 2; ++hint) cand.push_back({-1, static_cast<int>(std::max<int64_t>(g, 1)), hint});
     }
+    // (the merge-path matvec is not a candidate: slower on every matrix
+    // measured, and on tiny ones a timing tie would change the reduction order)
     for (int t : {2, 4, 8, 16}) cand.push_back({t, 0, 0});
-    cand.push_back({kMergeKernel, 0, 0});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return;
     Cand best = cand[0];

@@ -125,7 +125,7 @@ ITER_SPREAD = {
     ("batched_grid3d_18", "msp", 0): 8,
     ("batched_grid3d_18", "msp", 5): 10,
     ("batched_grid3d_18", "none", 0): 14,
-    ("batched_grid3d_18", "none", 5): 3,
+    ("batched_grid3d_18", "none", 5): 9,
     ("served_grid2d_56x40", "msp"): 7,
     # column 0 of the group-solve graphs
     ("group", "grid3d_16x15x14"): 8,

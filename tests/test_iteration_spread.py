@@ -89,9 +89,9 @@ def _variant(v, g, kind, b, mu, seed, coarse_max, krylov, restart, inner_tol, in
 
 
 def _spread(g, kind, b, *, mu=0.8, seed=17, coarse_max=32, krylov="cg", restart=30,
-            inner_tol=1e-6, inner_maxit=500):
+            inner_tol=1e-6, inner_maxit=500, runs=PERTURBED_RUNS):
     args = (g, kind, b, mu, seed, coarse_max, krylov, restart, inner_tol, inner_maxit)
-    futs = [_pool().submit(_variant, v, *args) for v in range(2 + PERTURBED_RUNS)]
+    futs = [_pool().submit(_variant, v, *args) for v in range(2 + runs)]
     res = [f.result() for f in futs]
     counts = [c for c, _ in res]
     return max(counts) - min(counts), counts
@@ -170,10 +170,12 @@ def test_spread_of_the_pegp_inner_benchmark_settings(side):
 @pytest.mark.parametrize("prec", ["msp", "none"])
 def test_spread_of_the_batched_columns(prec):
     """Columns 0 and 5 of the batched 18 x 17 x 16 grid: the batched solve
-    and a single solve of the same column round differently."""
+    and a single solve of the same column round differently.  Plain CG runs
+    about 2,500 iterations here, long enough for the spread to need more
+    samples: 14 perturbed runs (three leave column 5 at 3 of its 9)."""
     g = gg.grid3d(18, 17, 16, weights="loguniform", lo=1e-3, hi=1e3, seed=3)
     for j in (0, 5):
-        spread, counts = _spread(g, prec, gg.rhs(g.n, seed=40 + j))
+        spread, counts = _spread(g, prec, gg.rhs(g.n, seed=40 + j), runs=14 if prec == "none" else PERTURBED_RUNS)
         _check(("batched_grid3d_18", prec, j), spread, counts)
 
 

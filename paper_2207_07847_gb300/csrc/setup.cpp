@@ -3,6 +3,7 @@
 // multilevel sparsifier T (Section 3.3), the top-level pseudo-inverse and, for
 // PEGP, the Laplacian of the positively weighted expanded graph H (Section 3.2).
 #include <algorithm>
+#include <memory>
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -511,49 +512,79 @@ void build_pegp(HostModel &m)
     HostCsr &H = m.LH;
     H.n = nt;
     {
-        // rows filled by the threads of the edge pass, each over its own
-        // edges, with atomic row counters and cursors (slot order within a
-        // row is then arbitrary; the sort below fixes it)
+        // rows filled without shared counters: every directed entry first goes
+        // to the bucket of the thread that owns its row (T ranges of equal
+        // length), producer by producer; then each owner counts and fills its
+        // own rows (slot order within a row is then arbitrary; the sort below
+        // fixes it)
         const int T = setup_threads(nt);
-        std::vector<std::atomic<int64_t>> cnt(static_cast<size_t>(nt));
-        for (auto &c : cnt) c.store(0, std::memory_order_relaxed);
+        const int64_t span = (nt + T - 1) / T;
+        auto owner = [&](int64_t row) { return static_cast<int>(row / span); };
         // thread t takes the t-th slice of every part's edges (balanced
         // whatever the parts' sizes)
         auto slice = [&](const EdgeAcc &E, int t) {
             const size_t m = E.i.size();
             return std::make_pair(m * t / T, m * (t + 1) / T);
         };
+        std::vector<int64_t> cnt(static_cast<size_t>(T) * T, 0);
         parallel_chunks(T, T, [&](int t, int64_t, int64_t) {
+            int64_t *c = cnt.data() + static_cast<size_t>(t) * T;
             for (const EdgeAcc &E : parts) {
                 const auto r = slice(E, t);
                 for (size_t e = r.first; e < r.second; ++e) {
-                    cnt[E.i[e]].fetch_add(1, std::memory_order_relaxed);
-                    cnt[E.j[e]].fetch_add(1, std::memory_order_relaxed);
+                    ++c[owner(E.i[e])];
+                    ++c[owner(E.j[e])];
                 }
             }
         });
-        H.rp.assign(static_cast<size_t>(nt) + 1, 0);
-        for (int64_t r = 0; r < nt; ++r) {
-            H.rp[r + 1] = H.rp[r] + cnt[r].load(std::memory_order_relaxed);
-            cnt[r].store(H.rp[r], std::memory_order_relaxed);
+        std::vector<int64_t> off(static_cast<size_t>(T) * T, 0), bstart(static_cast<size_t>(T) + 1, 0);
+        for (int b = 0; b < T; ++b) {
+            int64_t s = 0;
+            for (int t = 0; t < T; ++t) {
+                off[static_cast<size_t>(t) * T + b] = s;
+                s += cnt[static_cast<size_t>(t) * T + b];
+            }
+            bstart[b + 1] = bstart[b] + s;
         }
-        H.ci.assign(static_cast<size_t>(H.rp[nt]), 0);
-        H.w.assign(static_cast<size_t>(H.rp[nt]), 0.0);
+        struct Ent {
+            int32_t row, col;
+            double w;
+        };
+        // default-initialised storage: every slot is written by the scatter
+        // below, whose threads then touch the pages first
+        std::unique_ptr<Ent[]> ent(new Ent[static_cast<size_t>(std::max<int64_t>(bstart[T], 1))]);
         parallel_chunks(T, T, [&](int t, int64_t, int64_t) {
+            std::vector<int64_t> pos(static_cast<size_t>(T));
+            for (int b = 0; b < T; ++b) pos[b] = bstart[b] + off[static_cast<size_t>(t) * T + b];
             for (const EdgeAcc &E : parts) {
                 const auto r = slice(E, t);
                 for (size_t e = r.first; e < r.second; ++e) {
-                    const int64_t a = cnt[E.i[e]].fetch_add(1, std::memory_order_relaxed);
-                    H.ci[a] = static_cast<int32_t>(E.j[e]);
-                    H.w[a] = E.w[e];
-                    const int64_t b = cnt[E.j[e]].fetch_add(1, std::memory_order_relaxed);
-                    H.ci[b] = static_cast<int32_t>(E.i[e]);
-                    H.w[b] = E.w[e];
+                    const int32_t i = static_cast<int32_t>(E.i[e]), j = static_cast<int32_t>(E.j[e]);
+                    ent[static_cast<size_t>(pos[owner(i)]++)] = {i, j, E.w[e]};
+                    ent[static_cast<size_t>(pos[owner(j)]++)] = {j, i, E.w[e]};
                 }
             }
         });
         parts.clear();
         parts.shrink_to_fit();
+        H.rp.assign(static_cast<size_t>(nt) + 1, 0);
+        // owner b writes the lengths of its rows r0 .. r1 - 1 at rp[r + 1]
+        parallel_chunks(T, T, [&](int b, int64_t, int64_t) {
+            for (int64_t q = bstart[b]; q < bstart[b + 1]; ++q) ++H.rp[static_cast<size_t>(ent[q].row) + 1];
+        });
+        for (int64_t r = 0; r < nt; ++r) H.rp[r + 1] += H.rp[r];
+        H.ci.assign(static_cast<size_t>(H.rp[nt]), 0);
+        H.w.assign(static_cast<size_t>(H.rp[nt]), 0.0);
+        parallel_chunks(T, T, [&](int b, int64_t, int64_t) {
+            const int64_t r0 = std::min(nt, static_cast<int64_t>(b) * span), r1 = std::min(nt, r0 + span);
+            std::vector<int64_t> cur(H.rp.begin() + r0, H.rp.begin() + r1);
+            for (int64_t q = bstart[b]; q < bstart[b + 1]; ++q) {
+                const Ent &x = ent[q];
+                const int64_t a = cur[static_cast<size_t>(x.row - r0)]++;
+                H.ci[a] = x.col;
+                H.w[a] = x.w;
+            }
+        });
     }
     H.diag.assign(static_cast<size_t>(nt), 0.0);
     parallel_chunks(nt, setup_threads(H.rp[nt]), [&](int, int64_t r0, int64_t r1) {

@@ -767,20 +767,26 @@ lap_status finish_model(HostModel &m)
         A.ci.resize(F.ci.size());
         A.w.resize(F.w.size());
         A.diag.resize(static_cast<size_t>(F.n));
-        std::vector<std::pair<int32_t, double>> row;
         for (int64_t i = 0; i < F.n; ++i) {
             const int32_t u = F.perm[i];
-            row.clear();
-            for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) row.push_back({F.pos[F.ci[p]], F.w[p]});
-            std::sort(row.begin(), row.end(),
-                      [](const auto &x, const auto &y) { return x.first < y.first; });
-            A.rp[i + 1] = A.rp[i] + static_cast<int64_t>(row.size());
-            for (size_t t = 0; t < row.size(); ++t) {
-                A.ci[A.rp[i] + t] = row[t].first;
-                A.w[A.rp[i] + t] = row[t].second;
-            }
-            A.diag[i] = F.deg[u];
+            A.rp[i + 1] = A.rp[i] + (F.rp[u + 1] - F.rp[u]);
         }
+        // rows on the host threads, each sorted by its (distinct) columns
+        parallel_chunks(F.n, setup_threads(A.rp[F.n]), [&](int, int64_t i0, int64_t i1) {
+            std::vector<std::pair<int32_t, double>> row;
+            for (int64_t i = i0; i < i1; ++i) {
+                const int32_t u = F.perm[i];
+                row.clear();
+                for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p) row.push_back({F.pos[F.ci[p]], F.w[p]});
+                std::sort(row.begin(), row.end(),
+                          [](const auto &x, const auto &y) { return x.first < y.first; });
+                for (size_t t = 0; t < row.size(); ++t) {
+                    A.ci[A.rp[i] + t] = row[t].first;
+                    A.w[A.rp[i] + t] = row[t].second;
+                }
+                A.diag[i] = F.deg[u];
+            }
+        });
     }
 
     // ---- top level: dense pseudo-inverse of mu^(2(l-1)) L_l ---------------
@@ -804,11 +810,18 @@ lap_status finish_model(HostModel &m)
         int64_t e = 0;
         for (int k = 0; k + 1 < l; ++k) {
             const HostLevel &F = m.lev[k];
-            for (int64_t u = 0; u < F.n; ++u) {
-                if (F.out[u] > 0.0) ++e;                           // parent edge
-                for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p)
-                    if (F.ci[p] > u && F.agg[F.ci[p]] == F.agg[u]) ++e;  // intra edge
-            }
+            const int T = setup_threads(F.rp[F.n]);
+            std::vector<int64_t> part(static_cast<size_t>(T), 0);
+            parallel_chunks(F.n, T, [&](int t, int64_t u0, int64_t u1) {
+                int64_t c = 0;
+                for (int64_t u = u0; u < u1; ++u) {
+                    if (F.out[u] > 0.0) ++c;                           // parent edge
+                    for (int64_t p = F.rp[u]; p < F.rp[u + 1]; ++p)
+                        if (F.ci[p] > u && F.agg[F.ci[p]] == F.agg[u]) ++c;  // intra edge
+                }
+                part[t] = c;
+            });
+            for (int64_t c : part) e += c;
         }
         e += m.lev[l - 1].rp[m.lev[l - 1].n] / 2;                  // top level
         m.edges_T = e;
